@@ -1,0 +1,272 @@
+"""Pins for the oracle's time stepping, adjoint and gradient (Sections 3.3-3.5):
+discrete energy conservation, the CFL bound, the adjoint dot-product test, central
+finite differences of the discrete misfit, the damping layer's reductions and
+absorption, the analytic 2D Green's function and a manufactured solution."""
+import numpy as np
+import pytest
+
+from oracle import analytic, assemble, kmv, wave
+from oracle import mesh as om
+from synth import meshes, signals
+
+
+def _sq_mesh(k, n, L=1.0, x0=0.0, y0=0.0, Ly=None):
+    V, C = meshes.structured_tri(n, n if Ly is None else int(round(n * Ly / L)), L,
+                                 L if Ly is None else Ly, x0, y0)
+    return om.Mesh(V, C, kmv.kmv_tri(k))
+
+
+def _layer_sigma(m, box, L, smax, faces):
+    """sigma_k = smax (d/L)^2 inside the layer on the listed faces (Section 2.1)."""
+    X = m.coords
+    s = np.zeros((m.N, m.dim))
+    for d in range(m.dim):
+        lo, hi = box[d]
+        if ("lo", d) in faces:
+            s[:, d] += np.where(X[:, d] < lo, ((lo - X[:, d]) / L) ** 2, 0.0)
+        if ("hi", d) in faces:
+            s[:, d] += np.where(X[:, d] > hi, ((X[:, d] - hi) / L) ** 2, 0.0)
+    return smax * s
+
+
+def test_ricker_closed_form_and_input_signal():
+    f = 5.0
+    t0 = 1 / f
+    assert analytic.ricker(t0, f) == 1.0
+    tz = t0 + 1 / (np.sqrt(2) * np.pi * f)
+    assert abs(analytic.ricker(tz, f)) < 1e-15
+    tt = np.linspace(0, 1, 101)
+    assert np.allclose(analytic.ricker(tt, f), analytic.ricker(2 * t0 - tt, f))
+    # the synthetic source signal fed to both paths is the same wavelet
+    dt = 1e-3
+    s = signals.ricker_samples(f, dt, 500)
+    assert np.allclose(s, analytic.ricker(np.arange(500) * dt, f), atol=1e-7)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_discrete_energy_is_conserved(k):
+    m = _sq_mesh(k, 6)
+    c = np.random.default_rng(0).uniform(1.5, 3.0, m.N)
+    ops = wave.Operators(m, c, 1.0)
+    dt = 0.9 * ops.cfl_dt()
+    ops = wave.Operators(m, c, dt)
+    X = m.coords
+    U_old = np.cos(np.pi * X[:, 0]) * np.cos(2 * np.pi * X[:, 1])
+    U = U_old.copy()
+    E0 = None
+    for n in range(300):
+        U_new = (-(ops.A0 @ U) - ops.A_minus * U_old) / ops.A_plus
+        En = ops.energy(U_new, U)
+        E0 = En if E0 is None else E0
+        assert abs(En - E0) < 1e-11 * abs(E0)
+        U_old, U = U, U_new
+
+
+def test_stability_below_and_blowup_above_cfl():
+    m = _sq_mesh(2, 6)
+    c = np.full(m.N, 1.5)
+    ops = wave.Operators(m, c, 1.0)
+    import scipy.sparse.linalg as spla
+    Minv = 1 / ops.M
+    L = spla.LinearOperator((m.N, m.N), matvec=lambda x: Minv * (ops.K @ x))
+    rho = abs(spla.eigs(L, k=1, which="LM", return_eigenvectors=False)[0])
+    rng = np.random.default_rng(1)
+
+    def run(dt, n=2000):
+        o = wave.Operators(m, c, dt)
+        U_old = rng.standard_normal(m.N)
+        U = U_old.copy()
+        for _ in range(n):
+            U_old, U = U, (-(o.A0 @ U) - o.A_minus * U_old) / o.A_plus
+        return np.abs(U).max()
+
+    assert run(0.9 * ops.cfl_dt()) < 10
+    assert run(1.02 * 2 / np.sqrt(rho), 400) > 1e6
+
+
+def _dot_test(ops, m, nt, src, recs):
+    H = assemble.point_matrix(m, recs)
+    rng = np.random.default_rng(7)
+    s = rng.standard_normal(nt)
+    rho = rng.standard_normal((nt + 1, H.shape[0]))
+    Fs, _ = ops.forward(wave.point_source_rhs(m, src, s), nt, H)
+    lam, _ = ops.adjoint(H, rho)
+    b = np.asarray(assemble.point_matrix(m, np.atleast_2d(src)).todense()).ravel()
+    lhs = np.sum(Fs * rho)
+    rhs = -np.sum(s * (lam[:nt] @ b))
+    return abs(lhs - rhs) / abs(lhs)
+
+
+@pytest.mark.parametrize("k,layer", [(2, False), (3, True), (4, True)])
+def test_adjoint_dot_product_2d(k, layer):
+    m = _sq_mesh(k, 8, L=1.5, x0=-0.25)
+    c = np.random.default_rng(2).uniform(1.5, 2.5, m.N)
+    sig = _layer_sigma(m, [(0.0, 1.0), (-1, 1.25)], 0.25, 30.0,
+                       {("lo", 0), ("hi", 0), ("hi", 1)}) if layer else None
+    dt = 0.8 * wave.Operators(m, c, 1.0).cfl_dt()
+    ops = wave.Operators(m, c, dt, sigma=sig, absorbing=layer)
+    err = _dot_test(ops, m, 120, [0.5, 0.3], np.array([[x, 0.7] for x in (0.1, 0.4, 0.9)]))
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_adjoint_dot_product_3d(k):
+    g = np.linspace(0, 1, 4)
+    V, C = meshes.kuhn_tets(g, g, g)
+    m = om.Mesh(V, C, kmv.kmv_tet(k))
+    c = np.random.default_rng(3).uniform(1.5, 2.5, m.N)
+    sig = _layer_sigma(m, [(0.2, 0.8), (0.2, 0.8), (-1, 0.7)], 0.2, 20.0,
+                       {("lo", 0), ("hi", 0), ("lo", 1), ("hi", 1), ("hi", 2)})
+    dt = 0.8 * wave.Operators(m, c, 1.0).cfl_dt()
+    ops = wave.Operators(m, c, dt, sigma=sig, absorbing=True)
+    err = _dot_test(ops, m, 60, [0.5, 0.5, 0.3], np.array([[0.3, 0.4, 0.6], [0.6, 0.5, 0.55]]))
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("k,layer", [(2, False), (3, True)])
+def test_gradient_matches_central_finite_differences(k, layer):
+    """delta^T M G (Eq. control_deriv) against (J(c+h delta) - J(c-h delta)) / 2h for
+    seeded smooth directions supported away from the boundary and the layer: the error
+    must fall as h^2 (the paper's one-sided Eq. discrete_fd only gives O(h))."""
+    m = _sq_mesh(k, 10, L=1.5, x0=-0.25)
+    X = m.coords
+    c = 1.5 + 0.5 * X[:, 1]
+    sig = _layer_sigma(m, [(0.0, 1.0), (-1, 1.25)], 0.25, 30.0,
+                       {("lo", 0), ("hi", 0), ("hi", 1)}) if layer else None
+    dt = 0.8 * wave.Operators(m, c, 1.0).cfl_dt()
+    nt = int(0.8 / dt)
+    src = [0.5, 0.1]
+    recs = np.array([[x, 1.0] for x in np.linspace(0.05, 0.95, 12)])
+    w = analytic.ricker(np.arange(nt) * dt, 5.0)
+    c_true = c * (1 + 0.08 * np.exp(-((X[:, 0] - 0.5) ** 2 + (X[:, 1] - 0.6) ** 2) / 0.02))
+    H = assemble.point_matrix(m, recs)
+
+    def J_of(cc):
+        o = wave.Operators(m, cc, dt, sigma=sig, absorbing=layer)
+        return o.forward(wave.point_source_rhs(m, src, w), nt, H, store=True)
+
+    obs, _ = J_of(c_true)
+    rec, U = J_of(c)
+    ops = wave.Operators(m, c, dt, sigma=sig, absorbing=layer)
+    _, g = ops.adjoint(H, rec - obs, U_hist=U)
+    G = ops.gradient(g)
+    inside = (X[:, 0] > 0.15) & (X[:, 0] < 0.85) & (X[:, 1] > 0.15) & (X[:, 1] < 0.85)
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        a, b, ph = rng.uniform(1, 4, 3)
+        delta = np.where(inside, np.sin(a * X[:, 0] + ph) * np.cos(b * X[:, 1]), 0.0)
+        dco = delta @ (ops.M * G)
+        errs = []
+        for h in (1e-2, 1e-3):
+            Jp = wave.misfit(J_of(c + h * delta)[0], obs)
+            Jm = wave.misfit(J_of(c - h * delta)[0], obs)
+            errs.append(abs((Jp - Jm) / (2 * h) - dco) / abs(dco))
+        assert errs[1] < 1e-5
+        assert errs[1] < errs[0] / 50  # second order
+
+
+def test_zero_damping_layer_reduces_to_plain_scheme():
+    m = _sq_mesh(3, 6)
+    c = np.full(m.N, 2.0)
+    dt = 0.8 * wave.Operators(m, c, 1.0).cfl_dt()
+    H = assemble.point_matrix(m, np.array([[0.3, 0.7], [0.8, 0.2]]))
+    w = analytic.ricker(np.arange(150) * dt, 6.0)
+    r0, _ = wave.Operators(m, c, dt).forward(wave.point_source_rhs(m, [0.5, 0.5], w), 150, H)
+    r1, _ = wave.Operators(m, c, dt, sigma=np.zeros((m.N, 2))).forward(
+        wave.point_source_rhs(m, [0.5, 0.5], w), 150, H)
+    assert np.array_equal(r0, r1)
+
+
+def _layer_case(layer, big=False, T=1.5):
+    L = 0.25
+    box = (-2.0, 3.0, 3.0) if big else (-L, 1 + L, 1 + L)
+    nper = 20
+    V, C = meshes.structured_tri(int((box[1] - box[0]) * nper), int(box[2] * nper),
+                                 box[1] - box[0], box[2], box[0], 0.0)
+    m = om.Mesh(V, C, kmv.kmv_tri(2))
+    c = np.full(m.N, 1.5)
+    sig = None
+    if layer and not big:
+        smax = 3 * 1.5 / (2 * L) * np.log(1e3)
+        sig = _layer_sigma(m, [(0.0, 1.0), (-1, 1.0)], L, smax, {("lo", 0), ("hi", 0), ("hi", 1)})
+    dt = 0.002
+    # the reference and the layered case absorb at the outer boundary; the no-layer case
+    # reflects everywhere (natural boundary)
+    ops = wave.Operators(m, c, dt, sigma=sig, absorbing=layer or big)
+    nt = int(T / dt)
+    H = assemble.point_matrix(m, np.array([[x, 0.3] for x in np.linspace(0.05, 0.95, 10)]))
+    w = analytic.ricker(np.arange(nt) * dt, 5.0)
+    rec, U = ops.forward(wave.point_source_rhs(m, [0.5, 0.1], w), nt, H, store=True)
+    return rec, U, ops
+
+
+def test_damping_layer_absorbs_and_energy_decays():
+    """Records with a 0.25 km layer against a domain large enough to have no side or
+    bottom reflections in the window: the layer must take the reflection at least 20 dB
+    below the no-layer case; after the source has stopped, the discrete energy must not
+    grow."""
+    ref, _, _ = _layer_case(False, big=True)
+    rec, U, ops = _layer_case(True)
+    rec0, _, _ = _layer_case(False)
+    e_layer = np.linalg.norm(rec - ref) / np.linalg.norm(ref)
+    e_none = np.linalg.norm(rec0 - ref) / np.linalg.norm(ref)
+    assert 20 * np.log10(e_none / e_layer) > 20
+    N = ops.mesh.N
+    energies = [ops.energy(U[n + 1], U[n]) for n in range(300, len(U) - 1)]
+    assert max(np.diff(energies)) <= 1e-12 * max(energies)
+
+
+@pytest.mark.slow
+def test_converges_to_image_sum_green_function():
+    """1 km box, c = 1.5 km/s, 5 Hz Ricker at the centre, Neumann walls: the receiver
+    error E (Eq. receiver_error_calc, trapezoid in time) against the method-of-images
+    Green's function falls under refinement and is below the paper's 5 % threshold."""
+    f, c0, T = 5.0, 1.5, 0.6
+    recs = np.array([[x, 0.9] for x in np.linspace(0.1, 0.9, 5)])
+    errs = []
+    for n in (16, 32):
+        V, C = meshes.structured_tri(n, n)
+        m = om.Mesh(V, C, kmv.kmv_tri(2))
+        c = np.full(m.N, c0)
+        dt = 0.25 * wave.Operators(m, c, 1.0).cfl_dt()
+        nt = int(round(T / dt))
+        ops = wave.Operators(m, c, dt)
+        H = assemble.point_matrix(m, recs)
+        w = analytic.ricker(np.arange(nt) * dt, f)
+        rec, _ = ops.forward(wave.point_source_rhs(m, [0.5, 0.5], w), nt, H)
+        t = np.arange(nt + 1) * dt
+        idx = np.arange(0, nt + 1, max(1, nt // 150))
+        ex = np.stack([analytic.box_image_sum(r, [0.5, 0.5], t[idx], c0, f, 1.0, 1.0)
+                       for r in recs], axis=1)
+        num = np.trapezoid(np.sum((rec[idx] - ex) ** 2, axis=1), t[idx])
+        den = np.trapezoid(np.sum(ex ** 2, axis=1), t[idx])
+        errs.append(np.sqrt(num / den))
+    assert errs[1] < 0.05
+    assert errs[1] < errs[0] / 2
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_manufactured_solution_converges(k):
+    """u = t^2 cos(pi x) cos(pi y) on the unit square with natural boundaries (the
+    method-of-manufactured-solutions check of Section 5.2.1, with cosines so that the
+    natural boundary condition holds): the lumped source b_i = M_i f(x_i, t_n) drives the
+    scheme; the nodal error at T falls under refinement of h and dt together."""
+    c0 = 1.3
+    errs = []
+    for n in (4, 8):
+        V, C = meshes.structured_tri(n, n)
+        m = om.Mesh(V, C, kmv.kmv_tri(k))
+        X = m.coords
+        sx = np.cos(np.pi * X[:, 0]) * np.cos(np.pi * X[:, 1])
+        c = np.full(m.N, c0)
+        dt = 0.005 / n
+        T = 0.5
+        nt = int(round(T / dt))
+        ops = wave.Operators(m, c, dt)
+        rhs = lambda it: ops.M * (2.0 + 2 * np.pi**2 * c0**2 * (it * dt) ** 2) * sx
+        H = assemble.point_matrix(m, np.array([[0.3, 0.4]]))
+        _, U = ops.forward(rhs, nt, H, store=True)
+        exact = (nt * dt) ** 2 * sx
+        errs.append(np.sqrt(np.sum(ops.M * (U[-1] - exact) ** 2) / np.sum(ops.M * exact ** 2)))
+    assert errs[1] < 0.002
+    assert errs[1] < errs[0] / 3
