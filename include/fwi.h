@@ -1,0 +1,151 @@
+/*
+ * fwi.h -- C ABI of the GB300 library for the explicit mass-lumped (KMV) acoustic
+ * time step of "Full waveform inversion using triangular waveform adapted meshes"
+ * (arXiv 2108.10946): forward solve, discrete adjoint solve and mesh-independent
+ * gradient on triangles (k = 2..5) and tetrahedra (k = 2, 3).
+ *
+ * Conventions for every entry point
+ *   - Return value: 0 on success, a negative errno-style code otherwise:
+ *       FWI_EINVAL  (-22)  bad argument: det J <= 0, unsupported k, point outside mesh,
+ *                          size mismatch, NULL handle
+ *       FWI_ENOMEM  (-12)  device or host allocation failed
+ *       FWI_ERANGE  (-34)  a non-finite value appeared in the wavefield
+ *       FWI_ECUDA   (-5)   a CUDA runtime call failed
+ *     fwi_last_error() copies a one-line description of the most recent failure of the
+ *     calling thread. Nothing aborts the process.
+ *   - Geometry/coordinate arrays (verts, cells, source and receiver positions, velocity)
+ *     are HOST arrays owned by the caller and only read during the call.
+ *   - Bulk signal arrays (wavelets, records, residuals, gradients) may be host or device
+ *     pointers: the library asks the CUDA runtime which one it is. Host arrays are staged
+ *     through library-owned device buffers with copies on the caller's stream.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *     asynchronous with respect to the host only when every bulk pointer is a device
+ *     pointer; otherwise they return after the copies back to host memory complete.
+ *   - All device state (mesh, wavefields, checkpoints) is owned by the library and freed
+ *     by fwi_batch_free / fwi_mesh_free. Handles are not thread-safe; distinct handles
+ *     may be used from distinct threads.
+ *   - Coordinates are (x, z) in 2D and (x, y, z) in 3D, with the last axis the depth.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FWI_EINVAL (-22)
+#define FWI_ENOMEM (-12)
+#define FWI_ERANGE (-34)
+#define FWI_ECUDA (-5)
+
+typedef struct fwi_mesh fwi_mesh;
+typedef struct fwi_batch fwi_batch;
+
+/* Per-mesh parameters.
+ *   dim, k           2 (k = 2..5) or 3 (k = 2, 3): KMVktri / KMVktet (Section 3.2, Figs.
+ *                    2dels and 3dels; k = 1 is excluded: Table gwpl shows it does not reach
+ *                    the error threshold).
+ *   dt               time step; <= 0 selects cfl_factor * 2 / sqrt(rho_Gershgorin(M^-1 K))
+ *                    (Eq. spectral, Section 3.3), recomputed by fwi_set_velocity.
+ *   cfl_factor       fraction of the Gershgorin bound (the paper uses 10-20 % below it).
+ *   nsteps           Nt: records hold Nt + 1 samples (t_n = n dt, n = 0..Nt).
+ *   box_lo, box_hi   the physical domain Omega_0 (first dim entries used).
+ *   layer_faces      bit 2*d: damping layer below box_lo[d]; bit 2*d+1: above box_hi[d].
+ *   layer_width      L; sigma_d(x) = sigma_max * (distance into the layer / L)^2 inside
+ *                    the layer on axis d (quadratic profile, Section 2.1).
+ *   absorbing        nonzero: lumped Clayton-Engquist term int_{dOmega} c u_t v on the
+ *                    whole outer boundary (Appendix A, M_{u,1}).
+ *   ckpt_stride      forward checkpoint spacing in steps for the adjoint's recompute.
+ *   water_speed      the gradient is zeroed where c < water_speed (Section 5.4: 1.51
+ *                    km/s) and inside the damping layer; <= 0 disables the speed test.
+ */
+typedef struct {
+  int dim;
+  int k;
+  double dt;
+  double cfl_factor;
+  int nsteps;
+  double box_lo[3];
+  double box_hi[3];
+  int layer_faces;
+  double layer_width;
+  double sigma_max;
+  int absorbing;
+  int ckpt_stride;
+  double water_speed;
+} fwi_params;
+
+/* Builds the DoF numbering, locality order and per-element geometry of a simplex mesh
+ * (Sections 3.2 and 4.6). verts: [nverts][dim] doubles; cells: [ncells][dim+1] vertex
+ * ids (int32). Every element must have det J > 0 (FWI_EINVAL otherwise). The mesh is
+ * uploaded to the current CUDA device. On success *out owns it. */
+int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, int64_t ncells,
+                    const fwi_params* params, fwi_mesh** out);
+
+/* Number of global DoFs N (vertex, edge, face and interior KMV nodes). */
+int fwi_num_dofs(const fwi_mesh* m, int64_t* n);
+
+/* Physical coordinates of the DoFs in the library's order: xyz[N][dim] (host). Values
+ * per DoF passed in or out of the library (velocity, gradient) use this order. */
+int fwi_dof_coords(const fwi_mesh* m, double* xyz);
+
+/* Reference element tabulation (host): nodes xhat[n][dim], lumping weights w[n]
+ * (summing to the reference volume 1/dim!), derivative matrices
+ * dhat[dim][n][n] = d phi_j / d xhat_d at node q ([d][q][j]). Any pointer may be NULL. */
+int fwi_element(const fwi_mesh* m, int* n, double* xhat, double* w, double* dhat);
+
+/* The same tabulation without a mesh or a GPU (host only): KMVktri (dim 2, k = 2..5) or
+ * KMVktet (dim 3, k = 2, 3); also returns the highest polynomial degree the lumping rule
+ * integrates exactly. Arrays sized as for fwi_element; any pointer may be NULL. */
+int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, double* dhat,
+                          int* exact_degree);
+
+/* Sets the P-wavespeed at the DoFs (Section 4.6: c varies inside an element), c[N] host
+ * doubles in the order of fwi_dof_coords, all > 0. Recomputes c^2, the lumped damping
+ * coefficients and, if params.dt <= 0, the time step. */
+int fwi_set_velocity(fwi_mesh* m, const double* c);
+
+/* The time step in use. */
+int fwi_get_dt(const fwi_mesh* m, double* dt);
+
+/* A batch of S shots sharing the mesh and a receiver spread (Section 4.3: the source is
+ * the transpose of receiver interpolation, b_{g(e,k)} = w(t) phi_k(x_s)).
+ * src[S][dim], rec[R][dim] host doubles; every point must lie in the mesh (FWI_EINVAL).
+ * Allocates the batch's device state: wavefields, damping-layer auxiliaries, forward
+ * checkpoints every ckpt_stride steps and a recompute ring of ckpt_stride wavefields. */
+int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const double* rec,
+                     fwi_batch** out);
+
+/* Forward solve, Eq. (forward3) with the readings documented in the design doc, for every shot
+ * of the batch. wavelet[S][Nt] floats (w(t_n), n = 0..Nt-1); rec_out[S][Nt+1][R] floats
+ * (d^n = H U^n). Stores the checkpoints the adjoint needs. */
+int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
+
+/* Discrete adjoint solve (Section 3.4, the transposed recurrence run backwards) driven by
+ * residual[S][Nt+1][R] = d - dtilde, with the forward wavefield recomputed segment by
+ * segment from the checkpoints of the last fwi_forward_shot. Accumulates the integrand of
+ * Eq. (gradient3), sum_n 2 c grad u^dagger . grad u, summed over the batch's shots, into
+ * the batch's compensated FP64 accumulator, and J = 1/2 sum residual^2. */
+int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream);
+
+/* G = M^{-1} g (Eq. gradient3), zeroed in the damping layer and where c < water_speed;
+ * grad_out[N] doubles in DoF order, misfit_out (may be NULL) the accumulated J. Clears
+ * the accumulators. */
+int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream);
+
+int fwi_batch_free(fwi_batch* b);
+int fwi_mesh_free(fwi_mesh* m);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to len). */
+int fwi_last_error(char* buf, int len);
+
+/* Kernel launches the library issued on this thread since the last call (counter read and
+ * reset). */
+int64_t fwi_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FWI_H */

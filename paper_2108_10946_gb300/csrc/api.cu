@@ -1,0 +1,1144 @@
+// Host side of the C ABI declared in include/fwi.h: mesh preparation (DoF numbering,
+// locality order, geometry, lumped mass, damping layer, CFL estimate), batches of shots,
+// and the time loops of the forward solve, the checkpointed adjoint solve and the gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <functional>
+#include <memory>
+#include <mutex>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fwi.h"
+#include "fwi_internal.h"
+#include "kmv_tab.h"
+
+using fwi::StepArgs;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int64_t g_launches = 0;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (x);                                                               \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? FWI_ENOMEM : FWI_ECUDA,             \
+                  std::string(#x) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return 0;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return fail(FWI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  return 0;
+}
+
+template <class T>
+int upload(T** p, const std::vector<T>& v) {
+  int rc = dalloc(p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f) {
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 4096) nt = 1;
+  std::vector<std::thread> th;
+  int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    int64_t a = t * chunk, b = std::min<int64_t>(n, a + chunk);
+    if (a >= b) break;
+    th.emplace_back([&, a, b] { f(a, b); });
+  }
+  for (auto& x : th) x.join();
+}
+
+uint64_t spread_bits(uint64_t x, int dims) {
+  uint64_t r = 0;
+  for (int b = 0; b < 21; ++b) r |= ((x >> b) & 1ull) << (b * dims);
+  return r;
+}
+
+struct KeyHash {
+  size_t operator()(const std::array<int64_t, 4>& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < 4; ++i) {
+      h ^= (uint64_t)k[i] + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    }
+    return h;
+  }
+};
+
+}  // namespace
+
+struct fwi_mesh {
+  fwi_params p;
+  int dim = 0, k = 0, nn = 0, ns = 0, ni = 0;
+  int device = 0;
+  kmvtab::Element el;
+  const fwi::KernelSet* ks = nullptr;
+  int64_t nverts = 0;
+  int E = 0, E0 = 0, N = 0, Ns = 0, Nl = 0;
+  std::vector<double> verts;
+  std::vector<int32_t> cells;      // user order
+  std::vector<int32_t> order;      // new element -> user element
+  std::vector<int32_t> conn;       // [E][nn] DoF of every local node (new order)
+  std::vector<double> dof_xyz;     // [N][dim]
+  std::vector<double> Jinv, detJ;  // [E][dim*dim] (row-major inverse), [E]
+  std::vector<double> M, Mb;       // [N]
+  std::vector<double> sigma;       // [N][dim]
+  std::vector<int32_t> pidx;       // [N]
+  std::vector<double> c;           // [N]
+  double dt = 0;
+  bool have_velocity = false;
+  // device
+  int* d_conn = nullptr;     // [ns][E]
+  float* d_geo = nullptr;    // [NG][E]
+  float* d_lgeo = nullptr;   // [dim*dim][E-E0]
+  int* d_pidx = nullptr;
+  float* d_c2 = nullptr;
+  float* d_c = nullptr;
+  float* d_cf = nullptr;     // [3][N]
+  float* d_lcf = nullptr;    // [Nl][count]
+  double* d_M = nullptr;
+  unsigned char* d_mask = nullptr;
+};
+
+struct fwi_batch {
+  fwi_mesh* m = nullptr;
+  int S = 0, log2S = 0, R = 0, nt = 0, K = 0, C = 0;
+  std::vector<int32_t> src_elem;   // [S] new element index
+  std::vector<float> src_phi;      // [S][nn]
+  std::vector<int32_t> rec_elem;   // [R]
+  std::vector<float> rec_phi;      // [R][nn]
+  // device
+  int* d_inj = nullptr;
+  int* d_src_elem = nullptr;
+  float* d_src_phi = nullptr;
+  int* d_rslot_ptr = nullptr;
+  int* d_rslot_rec = nullptr;
+  float* d_rslot_phi = nullptr;
+  int* d_rec_elem = nullptr;
+  float* d_rec_phi = nullptr;
+  float *u = nullptr, *v = nullptr, *r = nullptr;          // forward state [N][S]
+  float *P = nullptr, *Pacc = nullptr, *PaccY = nullptr;   // [Nl][dim][S]
+  float *Y = nullptr, *Yacc = nullptr;                     // [Nl][S]
+  float *ua = nullptr, *va = nullptr, *Pa = nullptr, *Ya = nullptr;  // adjoint state
+  float* ckpt = nullptr;   // C x state
+  float* ring = nullptr;   // K x [N][S]
+  float* gseg = nullptr;
+  double *gsum = nullptr, *gcomp = nullptr, *misfit = nullptr;
+  int* status = nullptr;
+  // staging for host pointers
+  float* wav_dev = nullptr;  // [S][nt] the forward's wavelet, re-injected by the recompute
+  float* stage_in = nullptr;
+  float* stage_out = nullptr;
+  double* stage_grad = nullptr;
+  bool forward_done = false;
+  size_t state_floats() const {
+    const fwi_mesh* mm = m;
+    return (size_t)S * (2 * (size_t)mm->N + (size_t)mm->Nl * (mm->dim + (mm->dim == 3 ? 1 : 0)));
+  }
+};
+
+namespace {
+
+int check_device(const fwi_mesh* m) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != m->device)
+    return fail(FWI_EINVAL, "the mesh's CUDA device is not the current device");
+  return 0;
+}
+
+// Upload the reference tables of (dim, k) to the constant memory of the current device.
+int ensure_constants(fwi_mesh* m) {
+  static std::vector<std::array<int, 3>> done;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& d : done)
+    if (d[0] == m->device && d[1] == m->dim && d[2] == m->k) return 0;
+  std::vector<float> dh(m->el.dhat.begin(), m->el.dhat.end()), w(m->el.w.begin(), m->el.w.end());
+  int e = m->ks->upload_constants(dh.data(), w.data());
+  if (e != 0) return fail(FWI_ECUDA, std::string("constant upload: ") + cudaGetErrorString((cudaError_t)e));
+  done.push_back({m->device, m->dim, m->k});
+  return 0;
+}
+
+double sigma_at(const fwi_params& p, int dim, const double* x, int d) {
+  double s = 0;
+  if (p.layer_width <= 0 || p.sigma_max <= 0) return 0;
+  if (p.layer_faces & (1 << (2 * d))) {
+    double dist = p.box_lo[d] - x[d];
+    if (dist > 0) s += (dist / p.layer_width) * (dist / p.layer_width);
+  }
+  if (p.layer_faces & (1 << (2 * d + 1))) {
+    double dist = x[d] - p.box_hi[d];
+    if (dist > 0) s += (dist / p.layer_width) * (dist / p.layer_width);
+  }
+  (void)dim;
+  return p.sigma_max * s;
+}
+
+// inverse of the column-edge Jacobian J (J[r][c] = x_{c+1,r} - x_{0,r}); returns det J
+double jac_inverse(int dim, const double* X /*[dim+1][dim]*/, double* inv /*[dim][dim]*/) {
+  double J[9];
+  for (int r = 0; r < dim; ++r)
+    for (int c = 0; c < dim; ++c) J[r * dim + c] = X[(c + 1) * dim + r] - X[r];
+  if (dim == 2) {
+    double det = J[0] * J[3] - J[1] * J[2];
+    inv[0] = J[3] / det;
+    inv[1] = -J[1] / det;
+    inv[2] = -J[2] / det;
+    inv[3] = J[0] / det;
+    return det;
+  }
+  double a = J[0], b = J[1], c = J[2], d = J[3], e = J[4], f = J[5], g = J[6], h = J[7], i = J[8];
+  double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
+  double det = a * A + b * B + c * C;
+  inv[0] = A / det;
+  inv[1] = -(b * i - c * h) / det;
+  inv[2] = (b * f - c * e) / det;
+  inv[3] = B / det;
+  inv[4] = (a * i - c * g) / det;
+  inv[5] = -(a * f - c * d) / det;
+  inv[6] = C / det;
+  inv[7] = -(a * h - b * g) / det;
+  inv[8] = (a * e - b * d) / det;
+  return det;
+}
+
+// Reference coordinates of x in element (user id) ue; returns min barycentric.
+double locate_in(const fwi_mesh* m, int ue, const double* x, double* xh) {
+  int d = m->dim;
+  double X[12], inv[9];
+  for (int v = 0; v <= d; ++v)
+    for (int c = 0; c < d; ++c) X[v * d + c] = m->verts[(size_t)m->cells[(size_t)ue * (d + 1) + v] * d + c];
+  jac_inverse(d, X, inv);
+  double lam0 = 1, mn = 1e300;
+  for (int r = 0; r < d; ++r) {
+    double s = 0;
+    for (int c = 0; c < d; ++c) s += inv[r * d + c] * (x[c] - X[c]);
+    xh[r] = s;
+    lam0 -= s;
+    mn = std::min(mn, s);
+  }
+  return std::min(mn, lam0);
+}
+
+// Point location: the lowest user element id whose barycentrics are all >= -1e-12.
+int locate(const fwi_mesh* m, const double* pts, int npts, std::vector<int>& user_elem,
+           std::vector<double>& xhat) {
+  int d = m->dim;
+  int E = m->E;
+  // uniform grid of element bounding boxes
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < m->nverts; ++v)
+    for (int c = 0; c < d; ++c) {
+      lo[c] = std::min(lo[c], m->verts[v * d + c]);
+      hi[c] = std::max(hi[c], m->verts[v * d + c]);
+    }
+  int nc = std::max(1, (int)std::pow((double)E / 4.0, 1.0 / d));
+  nc = std::min(nc, d == 2 ? 2048 : 256);
+  int ncell[3] = {nc, nc, d == 3 ? nc : 1};
+  auto cell_of = [&](const double* x, int c) {
+    double f = (x[c] - lo[c]) / (hi[c] - lo[c] + 1e-300) * ncell[c];
+    return std::max(0, std::min(ncell[c] - 1, (int)std::floor(f)));
+  };
+  std::vector<std::vector<int>> grid((size_t)ncell[0] * ncell[1] * ncell[2]);
+  for (int ue = 0; ue < E; ++ue) {
+    int cmin[3] = {0, 0, 0}, cmax[3] = {0, 0, 0};
+    double bl[3] = {1e300, 1e300, 1e300}, bh[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v <= d; ++v) {
+      const double* x = &m->verts[(size_t)m->cells[(size_t)ue * (d + 1) + v] * d];
+      for (int c = 0; c < d; ++c) {
+        bl[c] = std::min(bl[c], x[c]);
+        bh[c] = std::max(bh[c], x[c]);
+      }
+    }
+    for (int c = 0; c < d; ++c) {
+      cmin[c] = cell_of(bl, c);
+      cmax[c] = cell_of(bh, c);
+    }
+    for (int i = cmin[0]; i <= cmax[0]; ++i)
+      for (int j = cmin[1]; j <= cmax[1]; ++j)
+        for (int k = cmin[2]; k <= cmax[2]; ++k)
+          grid[((size_t)i * ncell[1] + j) * ncell[2] + k].push_back(ue);
+  }
+  user_elem.assign(npts, -1);
+  xhat.assign((size_t)npts * d, 0);
+  for (int p = 0; p < npts; ++p) {
+    const double* x = pts + (size_t)p * d;
+    int ci[3] = {0, 0, 0};
+    for (int c = 0; c < d; ++c) ci[c] = cell_of(x, c);
+    int best = -1;
+    double xh[3];
+    for (int ue : grid[((size_t)ci[0] * ncell[1] + ci[1]) * ncell[2] + ci[2]]) {
+      if (best >= 0 && ue > best) continue;
+      if (locate_in(m, ue, x, xh) >= -1e-12) best = ue;
+    }
+    if (best < 0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "point %d (%g, %g%s) lies outside the mesh", p, x[0], x[1],
+               d == 3 ? ", ..." : "");
+      return fail(FWI_EINVAL, buf);
+    }
+    locate_in(m, best, x, xh);
+    user_elem[p] = best;
+    for (int c = 0; c < d; ++c) xhat[(size_t)p * d + c] = xh[c];
+  }
+  return 0;
+}
+
+// Gershgorin bound of rho(M^-1 K) on the assembled stiffness (Eq. spectral).
+double gershgorin(const fwi_mesh* m) {
+  const int d = m->dim, n = m->nn, E = m->E;
+  const auto& el = m->el;
+  // element stiffness row a: K_e[a][b] = sum_q w_q |J| c_q^2 (Jinv^T Dhat[.,q,a]) . (Jinv^T Dhat[.,q,b])
+  auto row = [&](int e, int a, double* out) {
+    const double* Ji = &m->Jinv[(size_t)e * d * d];
+    const double det = m->detJ[e];
+    for (int b = 0; b < n; ++b) out[b] = 0;
+    for (int q = 0; q < n; ++q) {
+      const double c = m->c[m->conn[(size_t)e * n + q]];
+      const double wq = el.w[q] * std::fabs(det) * c * c;
+      double ga[3] = {0, 0, 0};
+      for (int r = 0; r < d; ++r)
+        for (int s = 0; s < d; ++s) ga[r] += Ji[s * d + r] * el.dhat[(s * n + q) * n + a];
+      for (int b = 0; b < n; ++b) {
+        double dot = 0;
+        for (int r = 0; r < d; ++r) {
+          double gb = 0;
+          for (int s = 0; s < d; ++s) gb += Ji[s * d + r] * el.dhat[(s * n + q) * n + b];
+          dot += ga[r] * gb;
+        }
+        out[b] += wq * dot;
+      }
+    }
+  };
+  // incidence of shared DoFs
+  std::vector<int64_t> ptr(m->Ns + 1, 0);
+  for (int e = 0; e < E; ++e)
+    for (int a = 0; a < m->ns; ++a) ptr[m->conn[(size_t)e * n + a] + 1]++;
+  for (int i = 0; i < m->Ns; ++i) ptr[i + 1] += ptr[i];
+  std::vector<int64_t> fillp(ptr.begin(), ptr.end() - 1);
+  std::vector<int32_t> inc((size_t)ptr[m->Ns] * 2);
+  for (int e = 0; e < E; ++e)
+    for (int a = 0; a < m->ns; ++a) {
+      int i = m->conn[(size_t)e * n + a];
+      int64_t pos = fillp[i]++;
+      inc[pos * 2] = e;
+      inc[pos * 2 + 1] = a;
+    }
+  std::atomic<double> best{0.0};
+  auto upd = [&](double v) {
+    double cur = best.load();
+    while (v > cur && !best.compare_exchange_weak(cur, v)) {
+    }
+  };
+  parallel_for(m->Ns, [&](int64_t i0, int64_t i1) {
+    std::vector<double> rw(n);
+    std::vector<std::pair<int, double>> acc;
+    double loc = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+      acc.clear();
+      for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+        int e = inc[t * 2], a = inc[t * 2 + 1];
+        row(e, a, rw.data());
+        for (int b = 0; b < n; ++b) acc.push_back({m->conn[(size_t)e * n + b], rw[b]});
+      }
+      std::sort(acc.begin(), acc.end(),
+                [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; });
+      double s = 0;
+      for (size_t t = 0; t < acc.size();) {
+        double v = 0;
+        size_t u = t;
+        while (u < acc.size() && acc[u].first == acc[t].first) v += acc[u++].second;
+        s += std::fabs(v);
+        t = u;
+      }
+      loc = std::max(loc, s / m->M[i]);
+    }
+    upd(loc);
+  });
+  parallel_for(E, [&](int64_t e0, int64_t e1) {
+    std::vector<double> rw(n);
+    double loc = 0;
+    for (int64_t e = e0; e < e1; ++e)
+      for (int a = m->ns; a < n; ++a) {
+        row((int)e, a, rw.data());
+        double s = 0;
+        for (int b = 0; b < n; ++b) s += std::fabs(rw[b]);
+        loc = std::max(loc, s / m->M[m->conn[(size_t)e * n + a]]);
+      }
+    upd(loc);
+  });
+  return best.load();
+}
+
+}  // namespace
+
+extern "C" {
+
+int fwi_last_error(char* buf, int len) {
+  if (!buf || len <= 0) return FWI_EINVAL;
+  snprintf(buf, (size_t)len, "%s", g_err.c_str());
+  return 0;
+}
+
+int64_t fwi_launch_count(void) {
+  int64_t v = g_launches;
+  g_launches = 0;
+  return v;
+}
+
+int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, int64_t ncells,
+                    const fwi_params* params, fwi_mesh** out) {
+  if (!verts || !cells || !params || !out || nverts <= 0 || ncells <= 0)
+    return fail(FWI_EINVAL, "fwi_mesh_upload: null or empty input");
+  *out = nullptr;
+  const int d = params->dim;
+  if (d != 2 && d != 3) return fail(FWI_EINVAL, "dim must be 2 or 3");
+  if (ncells > (int64_t)INT32_MAX / 64) return fail(FWI_EINVAL, "too many cells");
+  const fwi::KernelSet* ks = fwi::kernel_set(d, params->k);
+  if (!ks) return fail(FWI_EINVAL, "unsupported (dim, k): triangles k = 2..5, tetrahedra k = 2, 3");
+  std::unique_ptr<fwi_mesh> m(new fwi_mesh());
+  m->p = *params;
+  if (m->p.ckpt_stride <= 0) m->p.ckpt_stride = 50;
+  if (m->p.cfl_factor <= 0) m->p.cfl_factor = 0.9;
+  m->dim = d;
+  m->k = params->k;
+  m->ks = ks;
+  CUDA_TRY(cudaGetDevice(&m->device));
+  std::string err;
+  if (!kmvtab::build(d, params->k, m->el, err)) return fail(FWI_EINVAL, "KMV tabulation: " + err);
+  if (m->el.n != ks->nn) return fail(FWI_EINVAL, "KMV tabulation node count mismatch");
+  const int n = m->nn = m->el.n;
+  m->ns = ks->ns;
+  m->ni = ks->ni;
+  for (int q = 0; q < m->ns; ++q)
+    if (m->el.entity[q] == kmvtab::INTERIOR) return fail(FWI_EINVAL, "node order mismatch");
+  m->nverts = nverts;
+  m->verts.assign(verts, verts + nverts * d);
+  m->cells.assign(cells, cells + ncells * (d + 1));
+  const int E = m->E = (int)ncells;
+  for (int64_t i = 0; i < ncells * (d + 1); ++i)
+    if (cells[i] < 0 || cells[i] >= nverts) return fail(FWI_EINVAL, "cell vertex id out of range");
+
+  // geometry (user order) and the layer flag of every element
+  std::vector<double> uJinv((size_t)E * d * d), udet(E);
+  std::vector<char> ulayer(E, 0);
+  std::vector<uint64_t> code(E);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < nverts; ++v)
+    for (int c = 0; c < d; ++c) {
+      lo[c] = std::min(lo[c], verts[v * d + c]);
+      hi[c] = std::max(hi[c], verts[v * d + c]);
+    }
+  int bad = -1;
+  for (int e = 0; e < E; ++e) {
+    double X[12];
+    double cen[3] = {0, 0, 0};
+    for (int v = 0; v <= d; ++v)
+      for (int c = 0; c < d; ++c) {
+        X[v * d + c] = verts[(size_t)cells[(size_t)e * (d + 1) + v] * d + c];
+        cen[c] += X[v * d + c] / (d + 1);
+      }
+    udet[e] = jac_inverse(d, X, &uJinv[(size_t)e * d * d]);
+    if (!(udet[e] > 0) && bad < 0) bad = e;
+    for (int v = 0; v <= d; ++v)
+      for (int c = 0; c < d; ++c)
+        if (sigma_at(m->p, d, &X[v * d], c) > 0) ulayer[e] = 1;
+    uint64_t cc = 0;
+    for (int c = 0; c < d; ++c) {
+      double f = (cen[c] - lo[c]) / (hi[c] - lo[c] + 1e-300);
+      uint64_t qv = (uint64_t)std::min(2097151.0, std::max(0.0, f * 2097151.0));
+      cc |= spread_bits(qv, d) << c;
+    }
+    code[e] = cc;
+  }
+  if (bad >= 0) return fail(FWI_EINVAL, "element " + std::to_string(bad) + " has det J <= 0");
+  m->order.resize(E);
+  for (int e = 0; e < E; ++e) m->order[e] = e;
+  std::stable_sort(m->order.begin(), m->order.end(), [&](int a, int b) {
+    if (ulayer[a] != ulayer[b]) return ulayer[a] < ulayer[b];
+    return code[a] < code[b];
+  });
+  m->E0 = 0;
+  while (m->E0 < E && !ulayer[m->order[m->E0]]) ++m->E0;
+  m->Jinv.resize((size_t)E * d * d);
+  m->detJ.resize(E);
+  for (int e = 0; e < E; ++e) {
+    int ue = m->order[e];
+    std::copy(&uJinv[(size_t)ue * d * d], &uJinv[(size_t)ue * d * d] + d * d, &m->Jinv[(size_t)e * d * d]);
+    m->detJ[e] = udet[ue];
+  }
+
+  // DoF numbering: shared nodes by first touch (entity keys), interior nodes per element
+  const auto& el = m->el;
+  int nedge_nodes = 0, nface_nodes = 0;
+  for (int q = 0; q < n; ++q) {
+    nedge_nodes += el.entity[q] == kmvtab::EDGE;
+    nface_nodes += el.entity[q] == kmvtab::FACE;
+  }
+  nedge_nodes /= d == 2 ? 3 : 6;
+  if (d == 3) nface_nodes /= 4;
+  std::unordered_map<std::array<int64_t, 4>, int32_t, KeyHash> keys;
+  keys.reserve((size_t)E * m->ns / 2);
+  m->conn.assign((size_t)E * n, -1);
+  int32_t next = 0;
+  for (int e = 0; e < E; ++e) {
+    const int32_t* cv = &cells[(size_t)m->order[e] * (d + 1)];
+    for (int q = 0; q < m->ns; ++q) {
+      std::array<int64_t, 4> key = {0, 0, 0, 0};
+      const int* ev = &el.ent_verts[q * 3];
+      if (el.entity[q] == kmvtab::VERTEX) {
+        key = {0, cv[ev[0]], 0, 0};
+      } else if (el.entity[q] == kmvtab::EDGE) {
+        int64_t ga = cv[ev[0]], gb = cv[ev[1]];
+        int rank = el.ent_rank[q];
+        if (ga > gb) rank = nedge_nodes - 1 - rank;
+        key = {1, std::min(ga, gb), std::max(ga, gb), rank};
+      } else {
+        int64_t g[3] = {cv[ev[0]], cv[ev[1]], cv[ev[2]]};
+        int64_t dom = nface_nodes == 1 ? 0 : g[el.ent_rank[q]];
+        std::sort(g, g + 3);
+        key = {2 + 4 * dom, g[0], g[1], g[2]};
+      }
+      auto it = keys.find(key);
+      if (it == keys.end()) it = keys.emplace(key, next++).first;
+      m->conn[(size_t)e * n + q] = it->second;
+    }
+  }
+  m->Ns = next;
+  if ((int64_t)m->Ns + (int64_t)E * m->ni > INT32_MAX) return fail(FWI_EINVAL, "too many DoFs");
+  m->N = m->Ns + E * m->ni;
+  for (int e = 0; e < E; ++e)
+    for (int j = 0; j < m->ni; ++j) m->conn[(size_t)e * n + m->ns + j] = m->Ns + e * m->ni + j;
+  const int N = m->N;
+
+  // DoF coordinates, lumped mass, damping profile
+  m->dof_xyz.assign((size_t)N * d, 0);
+  std::vector<char> seen(N, 0);
+  m->M.assign(N, 0);
+  for (int e = 0; e < E; ++e) {
+    const int32_t* cv = &cells[(size_t)m->order[e] * (d + 1)];
+    for (int q = 0; q < n; ++q) {
+      int i = m->conn[(size_t)e * n + q];
+      m->M[i] += el.w[q] * m->detJ[e];
+      if (!seen[i]) {
+        seen[i] = 1;
+        for (int c = 0; c < d; ++c) {
+          double x = 0;
+          for (int v = 0; v <= d; ++v) x += el.bary[q * (d + 1) + v] * verts[(size_t)cv[v] * d + c];
+          m->dof_xyz[(size_t)i * d + c] = x;
+        }
+      }
+    }
+  }
+  m->sigma.assign((size_t)N * d, 0);
+  m->pidx.assign(N, -1);
+  m->Nl = 0;
+  for (int i = 0; i < N; ++i) {
+    bool any = false;
+    for (int c = 0; c < d; ++c) {
+      m->sigma[(size_t)i * d + c] = sigma_at(m->p, d, &m->dof_xyz[(size_t)i * d], c);
+      any |= m->sigma[(size_t)i * d + c] > 0;
+    }
+    if (any) m->pidx[i] = m->Nl++;
+  }
+  // lumped boundary mass: facets owned by one element
+  m->Mb.assign(N, 0);
+  if (m->p.absorbing) {
+    std::unordered_map<std::array<int64_t, 4>, int, KeyHash> fcount;
+    fcount.reserve((size_t)E * (d + 1));
+    for (int e = 0; e < E; ++e) {
+      const int32_t* cv = &cells[(size_t)m->order[e] * (d + 1)];
+      for (int i = 0; i <= d; ++i) {
+        std::array<int64_t, 4> key = {-1, -1, -1, -1};
+        int c = 0;
+        for (int v = 0; v <= d; ++v)
+          if (v != i) key[c++] = cv[v];
+        std::sort(key.begin(), key.begin() + d);
+        fcount[key]++;
+      }
+    }
+    const double ref = d == 2 ? 1.0 : 0.5;
+    for (int e = 0; e < E; ++e) {
+      const int32_t* cv = &cells[(size_t)m->order[e] * (d + 1)];
+      for (int i = 0; i <= d; ++i) {
+        std::array<int64_t, 4> key = {-1, -1, -1, -1};
+        int c = 0;
+        int fv[3];
+        for (int v = 0; v <= d; ++v)
+          if (v != i) {
+            fv[c] = cv[v];
+            key[c++] = cv[v];
+          }
+        std::sort(key.begin(), key.begin() + d);
+        if (fcount[key] != 1) continue;
+        double meas;
+        const double* a = &verts[(size_t)fv[0] * d];
+        const double* b = &verts[(size_t)fv[1] * d];
+        if (d == 2) {
+          meas = std::hypot(b[0] - a[0], b[1] - a[1]);
+        } else {
+          const double* cc = &verts[(size_t)fv[2] * d];
+          double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+          double w[3] = {cc[0] - a[0], cc[1] - a[1], cc[2] - a[2]};
+          double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+          meas = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        }
+        const auto& fn = el.facet_nodes[i];
+        for (size_t t = 0; t < fn.size(); ++t)
+          m->Mb[m->conn[(size_t)e * n + fn[t]]] += el.facet_weights[i][t] * meas / ref;
+      }
+    }
+  }
+
+  // device geometry
+  const int NG = d == 2 ? 3 : 6;
+  std::vector<float> geo((size_t)NG * E), lgeo((size_t)d * d * (E - m->E0));
+  for (int e = 0; e < E; ++e) {
+    const double* Ji = &m->Jinv[(size_t)e * d * d];
+    const double det = m->detJ[e];
+    double Gm[9];
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        double s = 0;
+        for (int t = 0; t < d; ++t) s += Ji[r * d + t] * Ji[c * d + t];
+        Gm[r * d + c] = det * s;  // |J| J^-1 J^-T
+      }
+    if (d == 2) {
+      geo[0 * (size_t)E + e] = (float)Gm[0];
+      geo[1 * (size_t)E + e] = (float)Gm[1];
+      geo[2 * (size_t)E + e] = (float)Gm[3];
+    } else {
+      const int idx[6] = {0, 1, 2, 4, 5, 8};
+      for (int g = 0; g < 6; ++g) geo[(size_t)g * E + e] = (float)Gm[idx[g]];
+    }
+    if (e >= m->E0)
+      for (int c = 0; c < d * d; ++c) lgeo[(size_t)c * (E - m->E0) + (e - m->E0)] = (float)(det * Ji[c]);
+  }
+  std::vector<int> conn_dev((size_t)m->ns * E);
+  for (int e = 0; e < E; ++e)
+    for (int q = 0; q < m->ns; ++q) conn_dev[(size_t)q * E + e] = m->conn[(size_t)e * n + q];
+  int rc;
+  if ((rc = upload(&m->d_conn, conn_dev)) || (rc = upload(&m->d_geo, geo)) ||
+      (rc = upload(&m->d_lgeo, lgeo)) || (rc = upload(&m->d_pidx, m->pidx)) ||
+      (rc = upload(&m->d_M, m->M))) {
+    fwi_mesh_free(m.release());
+    return rc;
+  }
+  if ((rc = ensure_constants(m.get()))) {
+    fwi_mesh_free(m.release());
+    return rc;
+  }
+  *out = m.release();
+  return 0;
+}
+
+int fwi_num_dofs(const fwi_mesh* m, int64_t* n) {
+  if (!m || !n) return fail(FWI_EINVAL, "null argument");
+  *n = m->N;
+  return 0;
+}
+
+int fwi_dof_coords(const fwi_mesh* m, double* xyz) {
+  if (!m || !xyz) return fail(FWI_EINVAL, "null argument");
+  std::memcpy(xyz, m->dof_xyz.data(), m->dof_xyz.size() * sizeof(double));
+  return 0;
+}
+
+int fwi_element(const fwi_mesh* m, int* n, double* xhat, double* w, double* dhat) {
+  if (!m) return fail(FWI_EINVAL, "null mesh");
+  if (n) *n = m->nn;
+  if (xhat) std::memcpy(xhat, m->el.xhat.data(), m->el.xhat.size() * sizeof(double));
+  if (w) std::memcpy(w, m->el.w.data(), m->el.w.size() * sizeof(double));
+  if (dhat) std::memcpy(dhat, m->el.dhat.data(), m->el.dhat.size() * sizeof(double));
+  return 0;
+}
+
+int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, double* dhat,
+                          int* exact_degree) {
+  kmvtab::Element el;
+  std::string err;
+  if (!kmvtab::build(dim, k, el, err)) return fail(FWI_EINVAL, "KMV tabulation: " + err);
+  if (n) *n = el.n;
+  if (exact_degree) *exact_degree = el.exact_degree;
+  if (xhat) std::memcpy(xhat, el.xhat.data(), el.xhat.size() * sizeof(double));
+  if (w) std::memcpy(w, el.w.data(), el.w.size() * sizeof(double));
+  if (dhat) std::memcpy(dhat, el.dhat.data(), el.dhat.size() * sizeof(double));
+  return 0;
+}
+
+int fwi_set_velocity(fwi_mesh* m, const double* c) {
+  if (!m || !c) return fail(FWI_EINVAL, "null argument");
+  if (int rc = check_device(m)) return rc;
+  const int N = m->N, d = m->dim;
+  for (int i = 0; i < N; ++i)
+    if (!(c[i] > 0) || !std::isfinite(c[i])) return fail(FWI_EINVAL, "velocity must be positive and finite");
+  m->c.assign(c, c + N);
+  if (m->p.dt > 0) {
+    m->dt = m->p.dt;
+  } else {
+    double rho = gershgorin(m);
+    m->dt = m->p.cfl_factor * 2.0 / std::sqrt(rho);
+  }
+  const double dt = m->dt;
+  std::vector<float> c2(N), cv(N), cf((size_t)3 * N);
+  const int LC = fwi::layer_coef_count(d);
+  std::vector<float> lcf((size_t)m->Nl * LC, 0.f);
+  std::vector<unsigned char> mask(N);
+  for (int i = 0; i < N; ++i) {
+    const double* s = &m->sigma[(size_t)i * d];
+    double tr = 0, m3, det1 = 1;
+    for (int k = 0; k < d; ++k) tr += s[k];
+    if (d == 2) {
+      m3 = s[0] * s[1];
+    } else {
+      m3 = s[0] * s[1] + s[0] * s[2] + s[1] * s[2];
+      det1 = s[0] * s[1] * s[2];
+    }
+    const double a = tr + c[i] * m->Mb[i] / m->M[i];
+    const double den = 1.0 + 0.5 * a * dt;
+    c2[i] = (float)(c[i] * c[i]);
+    cv[i] = (float)c[i];
+    cf[i] = (float)((1.0 - 0.5 * a * dt) / den);
+    cf[(size_t)N + i] = (float)(dt * dt / (m->M[i] * den));
+    cf[(size_t)2 * N + i] = (float)(dt * dt * m3 / den);
+    const bool in_layer = m->pidx[i] >= 0;
+    mask[i] = (!in_layer && !(m->p.water_speed > 0 && c[i] < m->p.water_speed)) ? 1 : 0;
+    if (in_layer) {
+      float* L = &lcf[(size_t)m->pidx[i] * LC];
+      for (int k = 0; k < d; ++k) {
+        double others = tr - s[k];
+        double psi2 = s[k] - others;
+        double dk = 1.0 + 0.5 * dt * s[k];
+        L[k] = (float)((1.0 - 0.5 * dt * s[k]) / dk);
+        L[d + k] = (float)(dt * psi2 * c[i] * c[i] / (m->M[i] * dk));
+        L[2 * d + k] = (float)(dt / (m->M[i] * dk));
+        L[3 * d + k] = (float)(psi2 * c[i] * c[i]);
+        if (d == 3) {
+          double psi3 = 1;
+          for (int l = 0; l < 3; ++l)
+            if (l != k) psi3 *= s[l];
+          L[4 * d + k] = (float)(dt * psi3 * c[i] * c[i] / (m->M[i] * dk));
+          L[5 * d + k] = (float)(psi3 * c[i] * c[i]);
+        }
+      }
+      if (d == 3) {
+        L[6 * d + 0] = (float)(dt * dt * det1 / den);
+        L[6 * d + 1] = (float)(dt * dt / den);
+        L[6 * d + 2] = (float)(dt * det1);
+        L[6 * d + 3] = (float)(dt / m->M[i]);
+      }
+    }
+  }
+  dfree(m->d_c2);
+  dfree(m->d_c);
+  dfree(m->d_cf);
+  dfree(m->d_lcf);
+  dfree(m->d_mask);
+  m->d_c2 = m->d_c = m->d_cf = m->d_lcf = nullptr;
+  m->d_mask = nullptr;
+  int rc;
+  if ((rc = upload(&m->d_c2, c2)) || (rc = upload(&m->d_c, cv)) || (rc = upload(&m->d_cf, cf)) ||
+      (rc = upload(&m->d_lcf, lcf)) || (rc = upload(&m->d_mask, mask)))
+    return rc;
+  m->have_velocity = true;
+  return 0;
+}
+
+int fwi_get_dt(const fwi_mesh* m, double* dt) {
+  if (!m || !dt) return fail(FWI_EINVAL, "null argument");
+  if (!m->have_velocity) return fail(FWI_EINVAL, "call fwi_set_velocity first");
+  *dt = m->dt;
+  return 0;
+}
+
+int fwi_batch_free(fwi_batch* b) {
+  if (!b) return 0;
+  void* ptrs[] = {b->d_inj, b->d_src_elem, b->d_src_phi, b->d_rslot_ptr, b->d_rslot_rec,
+                  b->d_rslot_phi, b->d_rec_elem, b->d_rec_phi, b->u, b->v, b->r, b->P, b->Pacc,
+                  b->PaccY, b->Y, b->Yacc, b->ua, b->va, b->Pa, b->Ya, b->ckpt, b->ring,
+                  b->gseg, b->gsum, b->gcomp, b->misfit, b->status, b->wav_dev, b->stage_in, b->stage_out,
+                  b->stage_grad};
+  for (void* p : ptrs) dfree(p);
+  delete b;
+  return 0;
+}
+
+int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const double* rec,
+                     fwi_batch** out) {
+  if (!m || !out || nshots <= 0 || nshots > 32 || (nshots & (nshots - 1)) || nrec < 0 || !src ||
+      (nrec > 0 && !rec))
+    return fail(FWI_EINVAL, "fwi_batch_create: nshots must be a power of two <= 32, points non-null");
+  if (!m->have_velocity) return fail(FWI_EINVAL, "call fwi_set_velocity before creating a batch");
+  if (int rc = check_device(m)) return rc;
+  *out = nullptr;
+  std::unique_ptr<fwi_batch, int (*)(fwi_batch*)> b(new fwi_batch(), fwi_batch_free);
+  b->m = m;
+  b->S = nshots;
+  while ((1 << b->log2S) < nshots) ++b->log2S;
+  b->R = nrec;
+  b->nt = m->p.nsteps;
+  b->K = m->p.ckpt_stride;
+  b->C = (b->nt + b->K - 1) / b->K;
+  if (b->nt <= 0) return fail(FWI_EINVAL, "nsteps must be positive");
+  const int d = m->dim, n = m->nn, N = m->N, S = b->S;
+  // point location (new element index = position of the user element in the order)
+  std::vector<int> new_of_user(m->E);
+  for (int e = 0; e < m->E; ++e) new_of_user[m->order[e]] = e;
+  std::vector<int> ue;
+  std::vector<double> xh;
+  if (int rc = locate(m, src, nshots, ue, xh)) return rc;
+  b->src_elem.resize(S);
+  b->src_phi.resize((size_t)S * n);
+  std::vector<double> phi(n);
+  for (int s = 0; s < S; ++s) {
+    b->src_elem[s] = new_of_user[ue[s]];
+    m->el.basis(&xh[(size_t)s * d], phi.data());
+    for (int k = 0; k < n; ++k) b->src_phi[(size_t)s * n + k] = (float)phi[k];
+  }
+  b->rec_elem.resize(nrec);
+  b->rec_phi.resize((size_t)nrec * n);
+  if (nrec > 0) {
+    if (int rc = locate(m, rec, nrec, ue, xh)) return rc;
+    for (int r = 0; r < nrec; ++r) {
+      b->rec_elem[r] = new_of_user[ue[r]];
+      m->el.basis(&xh[(size_t)r * d], phi.data());
+      for (int k = 0; k < n; ++k) b->rec_phi[(size_t)r * n + k] = (float)phi[k];
+    }
+  }
+  // injection slots: every element holding a source or a receiver
+  std::vector<int> inj(m->E, -1);
+  std::vector<int> slot_elems;
+  auto slot_of = [&](int e) {
+    if (inj[e] < 0) {
+      inj[e] = (int)slot_elems.size();
+      slot_elems.push_back(e);
+    }
+    return inj[e];
+  };
+  for (int s = 0; s < S; ++s) slot_of(b->src_elem[s]);
+  for (int r = 0; r < nrec; ++r) slot_of(b->rec_elem[r]);
+  const int ns = (int)slot_elems.size();
+  std::vector<int> sptr(ns + 1, 0), srec;
+  std::vector<float> sphi;
+  std::vector<std::vector<int>> lists(ns);
+  for (int r = 0; r < nrec; ++r) lists[inj[b->rec_elem[r]]].push_back(r);
+  for (int t = 0; t < ns; ++t) {
+    sptr[t + 1] = sptr[t] + (int)lists[t].size();
+    for (int r : lists[t]) {
+      srec.push_back(r);
+      for (int k = 0; k < n; ++k) sphi.push_back(b->rec_phi[(size_t)r * n + k]);
+    }
+  }
+  if (srec.empty()) {
+    srec.push_back(0);
+    sphi.assign(n, 0.f);
+  }
+  std::vector<int> src_elem_dev(b->src_elem.begin(), b->src_elem.end());
+  std::vector<int> rec_elem_dev(b->rec_elem.begin(), b->rec_elem.end());
+  if (rec_elem_dev.empty()) rec_elem_dev.push_back(0);
+  std::vector<float> rec_phi_dev = b->rec_phi;
+  if (rec_phi_dev.empty()) rec_phi_dev.assign(n, 0.f);
+  int rc;
+  const size_t NS_ = (size_t)N * S, LS = (size_t)m->Nl * d * S, YS = (size_t)m->Nl * S;
+  if ((rc = upload(&b->d_inj, inj)) || (rc = upload(&b->d_src_elem, src_elem_dev)) ||
+      (rc = upload(&b->d_src_phi, b->src_phi)) || (rc = upload(&b->d_rslot_ptr, sptr)) ||
+      (rc = upload(&b->d_rslot_rec, srec)) || (rc = upload(&b->d_rslot_phi, sphi)) ||
+      (rc = upload(&b->d_rec_elem, rec_elem_dev)) || (rc = upload(&b->d_rec_phi, rec_phi_dev)) ||
+      (rc = dalloc(&b->u, NS_)) || (rc = dalloc(&b->v, NS_)) || (rc = dalloc(&b->r, NS_)) ||
+      (rc = dalloc(&b->P, LS)) || (rc = dalloc(&b->Pacc, LS)) || (rc = dalloc(&b->PaccY, LS)) ||
+      (rc = dalloc(&b->Y, YS)) || (rc = dalloc(&b->Yacc, YS)) || (rc = dalloc(&b->ua, NS_)) ||
+      (rc = dalloc(&b->va, NS_)) || (rc = dalloc(&b->Pa, LS)) || (rc = dalloc(&b->Ya, YS)) ||
+      (rc = dalloc(&b->ckpt, b->state_floats() * b->C)) ||
+      (rc = dalloc(&b->ring, NS_ * b->K)) || (rc = dalloc(&b->gseg, (size_t)N)) ||
+      (rc = dalloc(&b->gsum, (size_t)N)) || (rc = dalloc(&b->gcomp, (size_t)N)) ||
+      (rc = dalloc(&b->misfit, 1)) || (rc = dalloc(&b->status, 1)))
+    return rc;
+  CUDA_TRY(cudaMemset(b->r, 0, NS_ * sizeof(float)));
+  if (LS) {
+    CUDA_TRY(cudaMemset(b->Pacc, 0, LS * sizeof(float)));
+    CUDA_TRY(cudaMemset(b->PaccY, 0, LS * sizeof(float)));
+    CUDA_TRY(cudaMemset(b->Yacc, 0, YS * sizeof(float)));
+  }
+  CUDA_TRY(cudaMemset(b->gseg, 0, (size_t)N * sizeof(float)));
+  CUDA_TRY(cudaMemset(b->gsum, 0, (size_t)N * sizeof(double)));
+  CUDA_TRY(cudaMemset(b->gcomp, 0, (size_t)N * sizeof(double)));
+  CUDA_TRY(cudaMemset(b->misfit, 0, sizeof(double)));
+  CUDA_TRY(cudaMemset(b->status, 0, sizeof(int)));
+  *out = b.release();
+  return 0;
+}
+
+}  // extern "C"
+
+namespace {
+
+StepArgs base_args(fwi_batch* b) {
+  fwi_mesh* m = b->m;
+  StepArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.E = m->E;
+  a.E0 = m->E0;
+  a.S = b->S;
+  a.log2S = b->log2S;
+  a.Ns = m->Ns;
+  a.N = m->N;
+  a.nt = b->nt;
+  a.dt = (float)m->dt;
+  a.conn = m->d_conn;
+  a.geo = m->d_geo;
+  a.lgeo = m->d_lgeo;
+  a.c2 = m->d_c2;
+  a.cvel = m->d_c;
+  a.cf = m->d_cf;
+  a.pidx = m->d_pidx;
+  a.lcf = m->d_lcf;
+  a.r = b->r;
+  a.Pacc = b->Pacc;
+  a.PaccY = b->PaccY;
+  a.Yacc = b->Yacc;
+  a.inj = b->d_inj;
+  a.src_elem = b->d_src_elem;
+  a.src_phi = b->d_src_phi;
+  a.rslot_ptr = b->d_rslot_ptr;
+  a.rslot_rec = b->d_rslot_rec;
+  a.rslot_phi = b->d_rslot_phi;
+  a.R = b->R;
+  a.gseg = b->gseg;
+  a.status = b->status;
+  return a;
+}
+
+void run_step(fwi_batch* b, const StepArgs& a, cudaStream_t st) {
+  b->m->ks->launch_step(a, st);
+  fwi::launch_node_update(a, b->m->dim, st);
+  g_launches += 2;
+}
+
+// state pointers of checkpoint c: u, v, P, Y
+void ckpt_ptrs(fwi_batch* b, int c, float** u, float** v, float** P, float** Y) {
+  const fwi_mesh* m = b->m;
+  float* base = b->ckpt + b->state_floats() * (size_t)c;
+  const size_t NS_ = (size_t)m->N * b->S, LS = (size_t)m->Nl * m->dim * b->S;
+  *u = base;
+  *v = base + NS_;
+  *P = base + 2 * NS_;
+  *Y = base + 2 * NS_ + LS;
+}
+
+int copy_state(fwi_batch* b, float* du, float* dv, float* dP, float* dY, const float* su,
+               const float* sv, const float* sP, const float* sY, cudaStream_t st) {
+  const fwi_mesh* m = b->m;
+  const size_t NS_ = (size_t)m->N * b->S * sizeof(float);
+  const size_t LS = (size_t)m->Nl * m->dim * b->S * sizeof(float);
+  const size_t YS = (size_t)m->Nl * b->S * sizeof(float);
+  CUDA_TRY(cudaMemcpyAsync(du, su, NS_, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(dv, sv, NS_, cudaMemcpyDeviceToDevice, st));
+  if (LS) CUDA_TRY(cudaMemcpyAsync(dP, sP, LS, cudaMemcpyDeviceToDevice, st));
+  if (m->dim == 3 && YS) CUDA_TRY(cudaMemcpyAsync(dY, sY, YS, cudaMemcpyDeviceToDevice, st));
+  return 0;
+}
+
+int zero_state(fwi_batch* b, float* u, float* v, float* P, float* Y, cudaStream_t st) {
+  const fwi_mesh* m = b->m;
+  const size_t NS_ = (size_t)m->N * b->S * sizeof(float);
+  const size_t LS = (size_t)m->Nl * m->dim * b->S * sizeof(float);
+  const size_t YS = (size_t)m->Nl * b->S * sizeof(float);
+  CUDA_TRY(cudaMemsetAsync(u, 0, NS_, st));
+  CUDA_TRY(cudaMemsetAsync(v, 0, NS_, st));
+  if (LS) CUDA_TRY(cudaMemsetAsync(P, 0, LS, st));
+  if (YS) CUDA_TRY(cudaMemsetAsync(Y, 0, YS, st));
+  return 0;
+}
+
+int check_status(fwi_batch* b, cudaStream_t st) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, b->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaGetLastError());
+  if (h) {
+    cudaMemsetAsync(b->status, 0, sizeof(int), st);
+    return fail(FWI_ERANGE, "non-finite value in the wavefield (time step above the stability limit?)");
+  }
+  return 0;
+}
+
+// Forward steps n0 .. n1-1 on the batch's forward state; optional records and checkpoints.
+void forward_steps(fwi_batch* b, int n0, int n1, const float* wav, float* recs, bool ckpts,
+                   cudaStream_t st) {
+  StepArgs a = base_args(b);
+  a.mode = 0;
+  a.u = b->u;
+  a.v = b->v;
+  a.P = b->P;
+  a.Y = b->Y;
+  a.wavelet = wav;
+  a.rec = recs;
+  for (int n = n0; n < n1; ++n) {
+    if (ckpts && n % b->K == 0) {
+      float *cu, *cv, *cP, *cY;
+      ckpt_ptrs(b, n / b->K, &cu, &cv, &cP, &cY);
+      copy_state(b, cu, cv, cP, cY, b->u, b->v, b->P, b->Y, st);
+    }
+    a.n = n;
+    run_step(b, a, st);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* stream) {
+  if (!b || !wavelet) return fail(FWI_EINVAL, "fwi_forward_shot: null argument");
+  if (int rc = check_device(b->m)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t wn = (size_t)b->S * b->nt, rn = (size_t)b->S * (b->nt + 1) * b->R;
+  if (!b->wav_dev && dalloc(&b->wav_dev, wn)) return FWI_ENOMEM;
+  CUDA_TRY(cudaMemcpyAsync(b->wav_dev, wavelet, wn * sizeof(float),
+                           is_device_ptr(wavelet) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  const float* wav = b->wav_dev;
+  float* recs = rec_out;
+  const bool host_out = rec_out && !is_device_ptr(rec_out);
+  if (host_out) {
+    if (!b->stage_out && dalloc(&b->stage_out, rn ? rn : 1)) return FWI_ENOMEM;
+    recs = b->stage_out;
+  }
+  if (int rc = zero_state(b, b->u, b->v, b->P, b->Y, st)) return rc;
+  if (recs && rn) CUDA_TRY(cudaMemsetAsync(recs, 0, rn * sizeof(float), st));
+  forward_steps(b, 0, b->nt, wav, recs, true, st);
+  if (recs && b->R) {
+    StepArgs a = base_args(b);
+    a.u = b->u;
+    a.rec = recs;
+    a.n = b->nt;
+    b->m->ks->launch_record(a, b->d_rec_elem, b->d_rec_phi, st);
+    g_launches += 1;
+  }
+  if (host_out && rn) CUDA_TRY(cudaMemcpyAsync(rec_out, recs, rn * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (int rc = check_status(b, st)) return rc;
+  b->forward_done = true;
+  return 0;
+}
+
+int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream) {
+  if (!b || !residual) return fail(FWI_EINVAL, "fwi_adjoint_shot: null argument");
+  if (!b->forward_done) return fail(FWI_EINVAL, "fwi_adjoint_shot needs a preceding fwi_forward_shot");
+  if (int rc = check_device(b->m)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
+  const float* res = residual;
+  if (!is_device_ptr(residual)) {
+    const size_t wn = (size_t)b->S * b->nt;
+    if (!b->stage_in && dalloc(&b->stage_in, std::max(wn, rn))) return FWI_ENOMEM;
+    CUDA_TRY(cudaMemcpyAsync(b->stage_in, residual, rn * sizeof(float), cudaMemcpyHostToDevice, st));
+    res = b->stage_in;
+  }
+  fwi::launch_misfit(res, (int64_t)rn, b->misfit, st);
+  g_launches += 1;
+  StepArgs a = base_args(b);
+  a.mode = 1;
+  a.u = b->ua;
+  a.v = b->va;
+  a.P = b->Pa;
+  a.Y = b->Ya;
+  a.resid = res;
+  if (int rc = zero_state(b, b->ua, b->va, b->Pa, b->Ya, st)) return rc;
+  const int nt = b->nt;
+  // m = nt: lam^{nt} = 0 gives lam^{nt-1} from the last residual sample (no gradient term)
+  a.n = nt;
+  a.ring_u = nullptr;
+  run_step(b, a, st);
+  const size_t NS_ = (size_t)b->m->N * b->S;
+  for (int c = b->C - 1; c >= 0; --c) {
+    const int n0 = c * b->K, n1 = std::min(n0 + b->K, nt);
+    float *cu, *cv, *cP, *cY;
+    ckpt_ptrs(b, c, &cu, &cv, &cP, &cY);
+    if (int rc = copy_state(b, b->u, b->v, b->P, b->Y, cu, cv, cP, cY, st)) return rc;
+    CUDA_TRY(cudaMemcpyAsync(b->ring, b->u, NS_ * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    for (int n = n0; n < n1 - 1; ++n) {
+      forward_steps(b, n, n + 1, b->wav_dev, nullptr, false, st);
+      CUDA_TRY(cudaMemcpyAsync(b->ring + NS_ * (size_t)(n + 1 - n0), b->u, NS_ * sizeof(float),
+                               cudaMemcpyDeviceToDevice, st));
+    }
+    for (int mm = n1 - 1; mm >= std::max(n0, 1); --mm) {
+      a.n = mm;
+      a.ring_u = b->ring + NS_ * (size_t)(mm - n0);
+      run_step(b, a, st);
+    }
+    fwi::launch_fold(b->gseg, b->gsum, b->gcomp, b->m->N, st);
+    g_launches += 1;
+  }
+  return check_status(b, st);
+}
+
+int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream) {
+  if (!b || !grad_out) return fail(FWI_EINVAL, "fwi_gradient: null argument");
+  if (int rc = check_device(b->m)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = b->m->N;
+  double* out = grad_out;
+  const bool host = !is_device_ptr(grad_out);
+  if (host) {
+    if (!b->stage_grad && dalloc(&b->stage_grad, (size_t)N)) return FWI_ENOMEM;
+    out = b->stage_grad;
+  }
+  fwi::launch_finish_gradient(b->gsum, b->gcomp, nullptr, b->m->d_M, b->m->d_mask, out, N, st);
+  g_launches += 1;
+  if (host) CUDA_TRY(cudaMemcpyAsync(grad_out, out, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double J = 0;
+  CUDA_TRY(cudaMemcpyAsync(&J, b->misfit, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (misfit_out) *misfit_out = J;
+  CUDA_TRY(cudaMemsetAsync(b->gsum, 0, (size_t)N * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, (size_t)N * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->misfit, 0, sizeof(double), st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int fwi_mesh_free(fwi_mesh* m) {
+  if (!m) return 0;
+  void* ptrs[] = {m->d_conn, m->d_geo, m->d_lgeo, m->d_pidx, m->d_c2, m->d_c, m->d_cf,
+                  m->d_lcf, m->d_M, m->d_mask};
+  for (void* p : ptrs) dfree(p);
+  delete m;
+  return 0;
+}
+
+}  // extern "C"

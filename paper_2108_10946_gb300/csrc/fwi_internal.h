@@ -1,0 +1,88 @@
+// Internal declarations shared by the host side of the library and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwi {
+
+// Element-kernel arguments (one step of the forward, recompute or adjoint recurrence).
+// Layouts (S = shots of the batch, stored shot-interleaved so that the lanes of one
+// element read one contiguous run of S floats):
+//   wavefields u, v (increment), r (shared-DoF accumulator)       [N][S]
+//   element-interior DoF j of element e has global id Ns + e*NI + j (no connectivity)
+//   conn   [NS][E]  shared-node DoF ids (node-major, coalesced over elements)
+//   geo    [NG][E]  Ghat = |J| J^-1 J^-T (NG = 3 in 2D, 6 in 3D: xx, xy, yy / xx, xy, xz, yy,
+//                   yz, zz)
+//   lgeo   [D*D][Elayer]  A = |J| J^-1 (row-major) for the damping-layer elements
+//                   e >= E0 (indexed e - E0)
+//   pidx   [N] index into the layer arrays or -1
+//   P, Pacc          [Nl][D][S], Y / Yacc [Nl][S] (3D)
+struct StepArgs {
+  int E, E0, S, Ns, N;
+  int log2S;
+  int mode;            // 0 forward, 1 adjoint (with gradient when ring != null)
+  int n;               // time index (forward: step n -> n+1; adjoint: step m)
+  int nt;
+  float dt;
+  const int* conn;
+  const float* geo;
+  const float* lgeo;
+  const float* c2;     // [N]
+  const float* cvel;   // [N] c (gradient weight 2c)
+  const float* cf;     // [3][N]: c1, c2, c3 of the increment update
+  const int* pidx;     // [N]
+  const float* lcf;    // [Nl][LCF] layer coefficients (see layer_coef_layout)
+  float* u;
+  float* v;
+  float* r;
+  float* P;
+  float* Pacc;
+  float* Y;
+  float* Yacc;
+  float* PaccY;        // 3D forward: lumped gradient of Y (D_{omega,3} term)
+  // sources / receivers
+  const int* inj;          // [E] slot id or -1
+  const int* src_elem;     // [S]
+  const float* src_phi;    // [S][NN]
+  const float* wavelet;    // [S][nt]
+  const int* rslot_ptr;    // [nslot+1]
+  const int* rslot_rec;    // receiver ids
+  const float* rslot_phi;  // [entries][NN]
+  int R;
+  float* rec;              // forward records [S][nt+1][R] (may be null)
+  const float* resid;      // adjoint residual [S][nt+1][R]
+  // gradient
+  const float* ring_u;     // forward U^m [N][S] (null: no gradient this step)
+  float* gseg;             // [N] FP32 segment accumulator
+  int* status;             // bit 0: non-finite value seen
+};
+
+// Layer coefficients per layer DoF (floats):
+//   [0..D)      e1_k  = (1 - dt sigma_k/2) / (1 + dt sigma_k/2)
+//   [D..2D)     e2f_k = dt Psi2_kk c^2 / (M (1 + dt sigma_k/2))   forward Q U
+//   [2D..3D)    e2a_k = dt / (M (1 + dt sigma_k/2))                adjoint D^T lam
+//   [3D..4D)    psi2c2_k = Psi2_kk c^2                              adjoint gather scale
+//   3D only: [4D..5D) e3f_k = dt Psi3_kk c^2/(M(1+dt sigma_k/2)); [5D..6D) psi3c2_k;
+//            6D: c4 = dt^2 detPsi1 / (1 + a dt/2); 6D+1: c5 = dt^2/(1 + a dt/2);
+//            6D+2: dt detPsi1; 6D+3: dt / M
+inline int layer_coef_count(int dim) { return dim == 2 ? 4 * 2 : 6 * 3 + 4; }
+
+// Per-(dim,k) entry points, defined in the instantiation units.
+struct KernelSet {
+  int dim, k, nn, ns, ni;
+  int (*upload_constants)(const float* dhat, const float* w);  // [D][NN][NN], [NN]
+  void (*launch_step)(const StepArgs& a, cudaStream_t st);
+  void (*launch_record)(const StepArgs& a, const int* rec_elem, const float* rec_phi,
+                        cudaStream_t st);  // d^n for every receiver and shot
+};
+const KernelSet* kernel_set(int dim, int k);
+
+// Generic (dimension-only) kernels.
+void launch_node_update(const StepArgs& a, int dim, cudaStream_t st);
+void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, cudaStream_t st);
+void launch_finish_gradient(const double* gsum, const double* gcomp, const float* Minv_unused,
+                            const double* M, const unsigned char* mask, double* out, int64_t N,
+                            cudaStream_t st);
+void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st);
+
+}  // namespace fwi

@@ -1,0 +1,97 @@
+// Dimension-generic kernels: the shared-DoF update, the FP64 compensated gradient fold,
+// the final M^-1 scaling and mask of Eq. (gradient3), and the misfit reduction.
+#include "update.cuh"
+
+namespace fwi {
+
+extern const KernelSet kernels_2_2, kernels_2_3, kernels_2_4, kernels_2_5, kernels_3_2,
+    kernels_3_3;
+
+const KernelSet* kernel_set(int dim, int k) {
+  if (dim == 2) {
+    switch (k) {
+      case 2: return &kernels_2_2;
+      case 3: return &kernels_2_3;
+      case 4: return &kernels_2_4;
+      case 5: return &kernels_2_5;
+    }
+  } else if (dim == 3) {
+    switch (k) {
+      case 2: return &kernels_3_2;
+      case 3: return &kernels_3_3;
+    }
+  }
+  return nullptr;
+}
+
+void launch_node_update(const StepArgs& a, int dim, cudaStream_t st) {
+  const int64_t threads = (int64_t)a.Ns * a.S;
+  if (threads == 0) return;
+  const int bs = 256;
+  const unsigned blocks = (unsigned)((threads + bs - 1) / bs);
+  if (dim == 2)
+    node_kernel<2><<<blocks, bs, 0, st>>>(a);
+  else
+    node_kernel<3><<<blocks, bs, 0, st>>>(a);
+}
+
+// Kahan fold of the FP32 segment sum into (sum, comp); comp carries the lost low part
+// with the sign convention sum - comp ~ exact.
+__global__ void fold_kernel(float* __restrict__ gseg, double* __restrict__ gsum,
+                            double* __restrict__ gcomp, int64_t N) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double x = (double)gseg[i];
+  gseg[i] = 0.f;
+  const double s = gsum[i];
+  const double y = x - gcomp[i];
+  const double t = s + y;
+  gcomp[i] = (t - s) - y;
+  gsum[i] = t;
+}
+
+void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, cudaStream_t st) {
+  if (N == 0) return;
+  fold_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gseg, gsum, gcomp, N);
+}
+
+__global__ void finish_kernel(const double* __restrict__ gsum, const double* __restrict__ gcomp,
+                              const double* __restrict__ M, const unsigned char* __restrict__ mask,
+                              double* __restrict__ out, int64_t N) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  out[i] = mask[i] ? (gsum[i] - gcomp[i]) / M[i] : 0.0;
+}
+
+void launch_finish_gradient(const double* gsum, const double* gcomp, const float*,
+                            const double* M, const unsigned char* mask, double* out, int64_t N,
+                            cudaStream_t st) {
+  if (N == 0) return;
+  finish_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gsum, gcomp, M, mask, out, N);
+}
+
+// acc += 1/2 sum resid^2 (block reduction in FP64, one atomic per block)
+__global__ void misfit_kernel(const float* __restrict__ r, int64_t n, double* acc) {
+  __shared__ double part[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = r[i];
+    s += x * x;
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(acc, 0.5 * part[0]);
+}
+
+void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st) {
+  if (n == 0) return;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 1216);
+  misfit_kernel<<<blocks, 256, 0, st>>>(resid, n, acc);
+}
+
+}  // namespace fwi

@@ -1,0 +1,109 @@
+// Per-DoF increment update shared by the element kernels (element-interior DoFs) and the
+// node kernel (shared DoFs), and the node kernel itself.
+#pragma once
+#include "fwi_internal.h"
+
+namespace fwi {
+
+template <int D>
+struct LayerCoef {  // offsets inside one layer DoF's coefficient record
+  static constexpr int E1 = 0, E2F = D, E2A = 2 * D, PSI2 = 3 * D, E3F = 4 * D, PSI3 = 5 * D,
+                       C4 = 6 * D, C5 = 6 * D + 1, DTDET = 6 * D + 2, DTM = 6 * D + 3;
+  static constexpr int COUNT = D == 2 ? 4 * D : 6 * D + 4;
+};
+
+// Increment-form update of one DoF (shared by the element and node kernels):
+//   v' = c1 v - c2 y - c3 u  (- c4 Y^n in the 3D forward, + c5 lam_omega^m in the 3D adjoint)
+//   u' = u + v'
+// plus the layer auxiliaries of the DoF:
+//   forward  P_k' = e1_k P_k - e2f_k sU_k (+ e3f_k sY_k in 3D);  Y' = Y + dt u
+//   adjoint  nu_k' = e1_k nu_k - e2a_k sU_k;  lam_w' = lam_w - dt detPsi1 lam + (dt/M) yw
+template <int D>
+__device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, float y, float uo,
+                                           const float* sU, const float* sY, float yw) {
+  const int S = a.S;
+  const size_t i = (size_t)dof * S + s;
+  const float c1 = __ldg(a.cf + dof);
+  const float c2 = __ldg(a.cf + (size_t)a.N + dof);
+  const float c3 = __ldg(a.cf + 2 * (size_t)a.N + dof);
+  const float vo = a.v[i];
+  float vn = c1 * vo - c2 * y - c3 * uo;
+  const int pi = __ldg(a.pidx + dof);
+  if (pi >= 0) {
+    typedef LayerCoef<D> L;
+    const float* lc = a.lcf + (size_t)pi * L::COUNT;
+    if (a.mode == 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const size_t pk = ((size_t)pi * D + k) * S + s;
+        float pn = __ldg(lc + L::E1 + k) * a.P[pk] - __ldg(lc + L::E2F + k) * sU[k];
+        if constexpr (D == 3) pn += __ldg(lc + L::E3F + k) * sY[k];
+        a.P[pk] = pn;
+      }
+      if constexpr (D == 3) {
+        const size_t py = (size_t)pi * S + s;
+        const float yo = a.Y[py];
+        vn -= __ldg(lc + L::C4) * yo;
+        a.Y[py] = yo + a.dt * uo;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const size_t pk = ((size_t)pi * D + k) * S + s;
+        a.P[pk] = __ldg(lc + L::E1 + k) * a.P[pk] - __ldg(lc + L::E2A + k) * sU[k];
+      }
+      if constexpr (D == 3) {
+        const size_t py = (size_t)pi * S + s;
+        const float wo = a.Y[py];
+        vn += __ldg(lc + L::C5) * wo;
+        a.Y[py] = wo - __ldg(lc + L::DTDET) * uo + __ldg(lc + L::DTM) * yw;
+      }
+    }
+  }
+  a.v[i] = vn;
+  const float un = uo + vn;
+  a.u[i] = un;
+  if (!isfinite(un)) atomicOr(a.status, 1);
+}
+
+// Shared-DoF finish: y from the atomic accumulator, then the same update.
+template <int D>
+__global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t >> a.log2S;
+  const int s = (int)(t & (a.S - 1));
+  if (i >= a.Ns) return;
+  const size_t ix = (size_t)i * a.S + s;
+  const float y = a.r[ix];
+  a.r[ix] = 0.f;
+  const float uo = a.u[ix];
+  float sU[D], sY[D];
+  float yw = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
+  const int pi = __ldg(a.pidx + i);
+  if (pi >= 0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const size_t pk = ((size_t)pi * D + k) * a.S + s;
+      sU[k] = a.Pacc[pk];
+      a.Pacc[pk] = 0.f;
+      if constexpr (D == 3) {
+        if (a.mode == 0) {
+          sY[k] = a.PaccY[pk];
+          a.PaccY[pk] = 0.f;
+        }
+      }
+    }
+    if constexpr (D == 3) {
+      if (a.mode == 1) {
+        const size_t py = (size_t)pi * a.S + s;
+        yw = a.Yacc[py];
+        a.Yacc[py] = 0.f;
+      }
+    }
+  }
+  dof_update<D>(a, (int)i, s, y, uo, sU, sY, yw);
+}
+
+}  // namespace fwi

@@ -1,0 +1,121 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same
+seeded inputs. Seismograms must agree to 1e-5 relative L2 per shot and gradients to 1e-4
+(FP32 GPU vs FP64 oracle)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from parity_util import OracleCase, match_dofs, rel_l2  # noqa: E402
+from synth import meshes, models, signals  # noqa: E402
+
+REC_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2108_10946_gb300 as pkg
+    pkg.build()
+    pkg.load()
+    return pkg
+
+
+def _case2d(k, n=12, layer=False):
+    """Unit square (plus a 0.25 km layer on the sides and bottom when layer=True)."""
+    if layer:
+        V, C = meshes.structured_tri(int(1.5 * n), int(1.25 * n), 1.5, 1.25, -0.25, 0.0)
+        lay = dict(box=[(0.0, 1.0), (-10.0, 1.0)], faces=0b1011, width=0.25,
+                   smax=signals.sigma_max(2.4, 0.25))
+    else:
+        V, C = meshes.structured_tri(n, n)
+        lay = None
+    rng = np.random.default_rng(k)
+    inner = (V[:, 0] > V[:, 0].min() + 1e-9) & (V[:, 0] < V[:, 0].max() - 1e-9) & \
+            (V[:, 1] > 1e-9) & (V[:, 1] < V[:, 1].max() - 1e-9)
+    V = V.copy()
+    V[inner] += 0.2 / n * rng.uniform(-1, 1, (inner.sum(), 2))
+    return V, C, lay
+
+
+def _run_both(lib, V, C, k, lay, nt, srcs, recs, absorbing, grad=False, cfun=models.smooth2d,
+              f=8.0):
+    from oracle import wave
+    dim = V.shape[1]
+    # dt from the oracle's Gershgorin estimate, passed to both sides
+    probe = OracleCase(V, C, k, cfun, 1.0, 1, layer=lay, absorbing=absorbing)
+    dt = 0.8 * probe.ops.cfl_dt()
+    orc = OracleCase(V, C, k, cfun, dt, nt, layer=lay, absorbing=absorbing)
+    kw = {}
+    if lay is not None:
+        box = [tuple(b) for b in lay["box"]]
+        kw = dict(box=box, layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"])
+    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=absorbing, ckpt_stride=17, **kw)
+    xg = mesh.dof_coords()
+    perm = match_dofs(orc.mesh.coords, xg, 1.0)  # xg[perm] == oracle coords
+    mesh.set_velocity(cfun(xg))
+    S = len(srcs)
+    wav = np.stack([signals.ricker_samples(f, dt, nt, t0=1.2 / f) for _ in range(S)])
+    wav[1::2] *= -0.7
+    batch = lib.Batch(mesh, np.array(srcs), np.array(recs))
+    rec_gpu = torch.zeros((S, nt + 1, len(recs)), dtype=torch.float32, device="cuda")
+    batch.forward(torch.from_numpy(wav).cuda(), rec_gpu)
+    rec_gpu = rec_gpu.cpu().numpy()
+    rec_orc = [orc.forward(srcs[s], np.array(recs), wav[s].astype(np.float64))[0] for s in range(S)]
+    out = dict(rec_gpu=rec_gpu, rec_orc=rec_orc, dt=dt, mesh=mesh, orc=orc, perm=perm)
+    if grad:
+        ctrue = lambda X: cfun(X) * (1 + 0.05 * np.exp(-np.sum((X - X.mean(0)) ** 2, 1) / 0.02))
+        obs_case = OracleCase(V, C, k, ctrue, dt, nt, layer=lay, absorbing=absorbing)
+        res = np.stack([rec_orc[s] - obs_case.forward(srcs[s], np.array(recs), wav[s].astype(np.float64))[0]
+                        for s in range(S)]).astype(np.float32)
+        batch.adjoint(torch.from_numpy(res).cuda())
+        G = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+        J = batch.gradient(G)
+        G = G.cpu().numpy()
+        Go = orc.gradient(srcs, np.array(recs), [w.astype(np.float64) for w in wav],
+                          [r.astype(np.float64) for r in res])
+        out.update(G_gpu=G[perm], G_orc=Go, J=J, J_ref=0.5 * float(np.sum(res.astype(np.float64) ** 2)))
+    return out
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_forward_records_2d(lib, k):
+    V, C, lay = _case2d(k)
+    srcs = [[0.5, 0.3], [0.31, 0.62]]
+    recs = [[x, 0.85] for x in np.linspace(0.05, 0.95, 9)]
+    o = _run_both(lib, V, C, k, lay, 300, srcs, recs, absorbing=False)
+    for s in range(2):
+        err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
+        print(f"k={k} shot {s}: records rel-L2 = {err:.3e}")
+        assert err < REC_TOL
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_forward_and_gradient_2d_layer(lib, k):
+    V, C, lay = _case2d(k, n=12, layer=True)
+    srcs = [[0.5, 0.1], [0.2, 0.15]]
+    recs = [[x, 0.9] for x in np.linspace(0.05, 0.95, 11)]
+    o = _run_both(lib, V, C, k, lay, 260, srcs, recs, absorbing=True, grad=True)
+    for s in range(2):
+        err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
+        print(f"k={k} layer shot {s}: records rel-L2 = {err:.3e}")
+        assert err < REC_TOL
+    gerr = rel_l2(o["G_gpu"], o["G_orc"])
+    print(f"k={k} layer: gradient rel-L2 = {gerr:.3e}, J {o['J']:.6e} vs {o['J_ref']:.6e}")
+    assert gerr < GRAD_TOL
+    assert abs(o["J"] - o["J_ref"]) < 1e-10 * abs(o["J_ref"])
+    # masked entries are exactly zero on both sides
+    assert np.all(o["G_gpu"][~o["orc"].mask] == 0)
+
+
+def test_gershgorin_dt_matches_oracle(lib):
+    V, C, _ = _case2d(3)
+    mesh = lib.Mesh(V, C, 3, 10, dt=0.0, cfl_factor=0.8)
+    xg = mesh.dof_coords()
+    mesh.set_velocity(models.smooth2d(xg))
+    orc = OracleCase(V, C, 3, models.smooth2d, 1.0, 1)
+    assert abs(mesh.dt - 0.8 * orc.ops.cfl_dt()) < 1e-12 * mesh.dt
