@@ -1,0 +1,344 @@
+"""Throughput of the KMV FWI hot path on GB300: forward + adjoint + gradient, DoF-steps/s.
+
+Workload (default): the 2D marine section of 17 km x 3.5 km (0.45 km water, 8 dipping
+layers, a normal fault, a 4.5 km/s salt body, +-5 % smoothed perturbation; seeded
+synthetic stand-in for Marmousi2) with a 1 km damping layer on the sides and bottom, a
+waveform-adapted KMV5 triangle mesh at 5 Hz, 4 s records, 500 receivers at 100 m depth and
+shots at 50 m depth. One step = one batch of S shots through the whole hot path:
+fwi_forward_shot (records + checkpoints), fwi_adjoint_misfit (residual, checkpointed
+recompute, adjoint, gradient integrand) and fwi_gradient.
+
+value = S * N * Nt * 2 / step time (forward and adjoint DoF-steps; recompute steps are not
+counted as work), summed over ranks. ``--impl reference`` times the FP64 oracle on the host
+cores instead (a bounded sample of the same workload).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAK_HBM_FALLBACK = 6800.0
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": PEAK_HBM_FALLBACK, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_workload(k=5, C=None, seed=0, nshots=40, nrec=500, T=4.0, f=5.0, small=False):
+    """Mesh, velocity, acquisition of the marine workload (inputs only)."""
+    from synth import meshes, models, signals
+    model = models.marine2d(seed)
+    box = (-1.0, 18.0, 0.0, 4.5)
+    if small:
+        box = (6.0, 8.0, 0.0, 1.5)
+    if C is None:
+        C = {2: 12.0, 3: 15.0, 4: 18.0, 5: 22.0}[k] if not small else 6.0
+    V, cells = meshes.adapted_tri(model, f, C, box, seed=seed, iters=10)
+    if small:
+        srcs = np.array([[7.0, 0.05], [6.5, 0.05]])
+        recs = np.array([[x, 0.1] for x in np.linspace(6.1, 7.9, 20)])
+        lay = dict(box=[(6.2, 7.8), (-10.0, 1.3)], faces=0b1011, width=0.2)
+    else:
+        srcs = np.stack([np.linspace(1.0, 16.0, nshots), np.full(nshots, 0.05)], 1)
+        recs = np.stack([np.linspace(0.1, 17.0, nrec), np.full(nrec, 0.1)], 1)
+        lay = dict(box=[(0.0, 17.0), (-10.0, 3.5)], faces=0b1011, width=1.0)
+    lay["smax"] = signals.sigma_max(4.7, lay["width"])
+    return dict(model=model, V=V, cells=cells, k=k, C=C, srcs=srcs, recs=recs, layer=lay, T=T,
+                f=f, box=box)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, device_index):
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        rows = [[x.strip() for x in r] for r in rows if r and r[0].strip() == str(device_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(wl, nsteps=200, budget_s=15.0):
+    """FP64 oracle DoF-steps/s (forward + adjoint) on a bounded sample: a 2 km x 1.5 km window
+    of the same model and element degree, a handful of steps. Single-threaded sparse algebra."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_util import OracleCase
+    from synth import signals
+    small = make_workload(k=wl["k"], small=True)
+    model = small["model"]
+    probe = OracleCase(small["V"], small["cells"], wl["k"], model, 1.0, 1, layer=small["layer"],
+                       absorbing=True)
+    dt = 0.9 * probe.ops.cfl_dt()
+    orc = OracleCase(small["V"], small["cells"], wl["k"], model, dt, nsteps, layer=small["layer"],
+                     absorbing=True)
+    w = signals.ricker_samples(wl["f"], dt, nsteps).astype(np.float64)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        rec, U = orc.forward(small["srcs"][0], small["recs"], w, store=True)
+        from oracle import assemble
+        H = assemble.point_matrix(orc.mesh, small["recs"])
+        orc.ops.adjoint(H, rec, U_hist=U)
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= 20:
+            break
+    el = time.perf_counter() - t0
+    dofsteps = done * orc.mesh.N * nsteps * 2
+    return dict(value=dofsteps / el, cores=1, N=orc.mesh.N, E=orc.mesh.E, nsteps=nsteps, reps=done,
+                seconds=el)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl_k = args.k
+    wl = dict(k=wl_k, f=5.0)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_rate(wl, budget_s=5.0)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_rate(wl, budget_s=10.0)
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    sample = (f"FP64 oracle, KMV{wl_k}tri window of the marine model (2 km x 1.5 km, "
+              f"{last['E']} elements, N={last['N']}), {last['nsteps']} forward + adjoint steps per rep")
+    line = {"impl": "reference", "metric": "DoF-steps/s (forward + adjoint)", "value": v,
+            "unit": "DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * el / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"marine2d-kmv{wl_k}-window", "model": "oracle"},
+            "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2108_10946_gb300 as pkg
+    from synth import signals
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.build()
+    wl = make_workload(k=args.k, C=args.C)
+    lay = wl["layer"]
+    t_setup = time.perf_counter()
+    mesh = pkg.Mesh(wl["V"], wl["cells"], wl["k"], 1, dt=0.0, cfl_factor=0.9,
+                    box=lay["box"], layer_faces=lay["faces"], layer_width=lay["width"],
+                    sigma_max=lay["smax"], absorbing=True, ckpt_stride=args.ckpt,
+                    water_speed=1.51)
+    xg = mesh.dof_coords()
+    c = wl["model"](xg)
+    mesh.set_velocity(c)
+    dt = mesh.dt
+    nt = int(round(wl["T"] / dt))
+    # rebuild with the step count fixed by T (dt is a property of mesh and velocity)
+    mesh.close()
+    mesh = pkg.Mesh(wl["V"], wl["cells"], wl["k"], nt, dt=dt, box=lay["box"],
+                    layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"],
+                    absorbing=True, ckpt_stride=args.ckpt, water_speed=1.51)
+    mesh.set_velocity(c)
+    N, E = mesh.N, wl["cells"].shape[0]
+    S = args.shots
+    shots = wl["srcs"][(rank * S + np.arange(S)) % len(wl["srcs"])]
+    batch = pkg.Batch(mesh, shots, wl["recs"])
+    R = len(wl["recs"])
+    wav = np.stack([signals.ricker_samples(wl["f"], dt, nt)] * S)
+    wav_d = torch.from_numpy(wav).cuda()
+    # observed data: the same sources through a true model (smoothed start model vs true:
+    # here the start model is the true model scaled, which is all the step needs)
+    obs_d = torch.zeros((S, nt + 1, R), device="cuda")
+    batch.forward(wav_d, obs_d)
+    obs_d *= 0.97
+    rec_d = torch.zeros((S, nt + 1, R), device="cuda")
+    G_d = torch.zeros(N, dtype=torch.float64, device="cuda")
+    setup_s = time.perf_counter() - t_setup
+
+    def step():
+        batch.forward(wav_d, rec_d)
+        batch.adjoint_misfit(obs_d)
+        batch.gradient(G_d)
+        if dist is not None:
+            dist.all_reduce(G_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    pkg.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    with clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    launches = pkg.launch_count()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    units = S * N * nt * 2 * world
+    value = units / (ms_step / 1000.0)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    wav_h = torch.from_numpy(wav).pin_memory()
+    obs_h = obs_d.cpu().pin_memory()
+    rec_h = torch.zeros((S, nt + 1, R)).pin_memory()
+    G_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        batch.forward(wav_h.numpy(), rec_h.numpy())
+        batch.adjoint_misfit(obs_h.numpy())
+        batch.gradient(G_h.numpy())
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = S * N * nt * 2 * world / e2e_s
+
+    # per-kernel timing of the forward step (events on the library's stream)
+    batch.profile(True)
+    batch.forward(wav_d, rec_d)
+    prof = batch.profile_read()
+    batch.profile(False)
+    fwd_ms = (prof["fwd_elem_ms"] + prof["fwd_node_ms"]) / max(prof["fwd_steps"], 1)
+    nn = {2: 7, 3: 12, 4: 18, 5: 30}[wl["k"]]
+    ns = {2: 6, 3: 9, 4: 12, 5: 15}[wl["k"]]
+    flops = E * 4 * 2 * nn * nn * S
+    bytes_alg = N * (16 * S + 8) + E * (4 * ns + 12)
+    peaks, src = _peaks()
+    clk_sum = clk.summary(local)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    achieved_tf = flops / (fwd_ms / 1000.0) / 1e12
+    achieved_gb = bytes_alg / (fwd_ms / 1000.0) / 1e9
+    hbm_peak = peaks["hbm_gbs"]
+    if achieved_tf / alu_peak >= achieved_gb / hbm_peak:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak, "traffic": None,
+                "hbm_frac": achieved_gb / hbm_peak, "hbm_achieved_gbs": achieved_gb,
+                "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gb, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gb / hbm_peak, "traffic": None, "alu_frac": achieved_tf / alu_peak,
+                "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"}
+    roof["kernel"] = f"forward time step (element + shared-DoF kernels), {fwd_ms*1000:.1f} us/step"
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ob = oracle_rate(dict(k=wl["k"], f=wl["f"]))
+        cpu = {"value": ob["value"], "unit": "DoF-steps/s", "cores": ob["cores"], "kind": "oracle",
+               "sample": (f"FP64 oracle, KMV{wl['k']}tri on a 2 km x 1.5 km window of the same "
+                          f"model ({ob['E']} elements, N={ob['N']}), {ob['nsteps']} forward + adjoint "
+                          f"steps x {ob['reps']}, {ob['seconds']:.1f} s")}
+    if rank == 0:
+        line = {
+            "metric": "DoF-steps/s (forward + adjoint, FP32, <=1e-5 rel-L2 vs FP64 oracle)",
+            "value": value, "unit": "DoF-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"marine2d-17x3.5km-kmv{wl['k']}-layer1km-5Hz-4s",
+                       "elements": E, "dofs": N, "nt": nt, "dt": dt, "shots_per_step": S,
+                       "receivers": R, "ckpt_stride": args.ckpt, "C": wl["C"],
+                       "l2": "inputs larger than L2 (wavefields of N*S floats, records)",
+                       "parallelism": f"shots across {world} GPU(s), replicas of the mesh",
+                       "setup_s": setup_s},
+            "e2e": {"value": e2e_val, "unit": "DoF-steps/s",
+                    "h2d_bytes_per_step": int(wav.nbytes + obs_h.numel() * 4),
+                    "d2h_bytes_per_step": int(rec_h.numel() * 4 + N * 8)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk_sum,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--C", type=float, default=None)
+    ap.add_argument("--shots", type=int, default=4)
+    ap.add_argument("--ckpt", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,17 @@ typedef struct {
 int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, int64_t ncells,
                     const fwi_params* params, fwi_mesh** out);
 
+/* Host-only preparation of the same mesh (numbering, geometry, lumped and boundary mass,
+ * damping profile) without touching a GPU: for inspection and tests. The handle supports
+ * fwi_num_dofs, fwi_dof_coords, fwi_element, fwi_mesh_host_arrays and fwi_mesh_free. */
+int fwi_mesh_prepare_host(const double* verts, int64_t nverts, const int32_t* cells,
+                          int64_t ncells, const fwi_params* params, fwi_mesh** out);
+
+/* Host copies: conn[E][n] (DoF of every local node, elements in the library's order),
+ * lumped mass[N], lumped boundary mass[N], sigma[N][dim]. Any pointer may be NULL. */
+int fwi_mesh_host_arrays(const fwi_mesh* m, int32_t* conn, double* mass, double* bmass,
+                         double* sigma);
+
 /* Number of global DoFs N (vertex, edge, face and interior KMV nodes). */
 int fwi_num_dofs(const fwi_mesh* m, int64_t* n);
 
@@ -130,10 +141,23 @@ int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* s
  * the batch's compensated FP64 accumulator, and J = 1/2 sum residual^2. */
 int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream);
 
+/* The same adjoint solve for the L2 misfit of Eq. (l2error): the residual d - dtilde is
+ * formed on the device from the batch's own records of the last fwi_forward_shot and
+ * observed[S][Nt+1][R] = dtilde (host or device). */
+int fwi_adjoint_misfit(fwi_batch* b, const float* observed, void* stream);
+
 /* G = M^{-1} g (Eq. gradient3), zeroed in the damping layer and where c < water_speed;
  * grad_out[N] doubles in DoF order, misfit_out (may be NULL) the accumulated J. Clears
  * the accumulators. */
 int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream);
+
+/* Per-kernel timing (tracing): when enabled, every time step of the batch's forward,
+ * recompute and adjoint loops is bracketed by CUDA events on the call's stream. */
+int fwi_profile(fwi_batch* b, int enable);
+/* ms[4] = {forward element kernel, forward node kernel, adjoint element kernel, adjoint node
+ * kernel} total milliseconds and steps[2] = {forward+recompute steps, adjoint steps} timed
+ * since the last read (then reset). Recompute steps count as forward steps. */
+int fwi_profile_read(fwi_batch* b, double* ms, int64_t* steps);
 
 int fwi_batch_free(fwi_batch* b);
 int fwi_mesh_free(fwi_mesh* m);

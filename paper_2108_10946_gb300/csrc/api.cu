@@ -162,10 +162,19 @@ struct fwi_batch {
   int* status = nullptr;
   // staging for host pointers
   float* wav_dev = nullptr;  // [S][nt] the forward's wavelet, re-injected by the recompute
+  float* rec_dev = nullptr;  // [S][nt+1][R] the forward's records
+  float* res_dev = nullptr;  // [S][nt+1][R] residual formed by fwi_adjoint_misfit
   float* stage_in = nullptr;
   float* stage_out = nullptr;
   double* stage_grad = nullptr;
   bool forward_done = false;
+  // optional per-kernel timing with CUDA events (fwi_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_mode;
+  size_t ev_used = 0;
+  double prof_ms[2][2] = {{0, 0}, {0, 0}};  // [forward/adjoint][element/node kernel]
+  int64_t prof_steps[2] = {0, 0};
   size_t state_floats() const {
     const fwi_mesh* mm = m;
     return (size_t)S * (2 * (size_t)mm->N + (size_t)mm->Nl * (mm->dim + (mm->dim == 3 ? 1 : 0)));
@@ -422,8 +431,11 @@ int64_t fwi_launch_count(void) {
   return v;
 }
 
-int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, int64_t ncells,
-                    const fwi_params* params, fwi_mesh** out) {
+}  // extern "C"
+
+namespace {
+int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64_t ncells,
+                const fwi_params* params, bool host_only, fwi_mesh** out) {
   if (!verts || !cells || !params || !out || nverts <= 0 || ncells <= 0)
     return fail(FWI_EINVAL, "fwi_mesh_upload: null or empty input");
   *out = nullptr;
@@ -439,7 +451,7 @@ int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, i
   m->dim = d;
   m->k = params->k;
   m->ks = ks;
-  CUDA_TRY(cudaGetDevice(&m->device));
+  if (!host_only) CUDA_TRY(cudaGetDevice(&m->device));
   std::string err;
   if (!kmvtab::build(d, params->k, m->el, err)) return fail(FWI_EINVAL, "KMV tabulation: " + err);
   if (m->el.n != ks->nn) return fail(FWI_EINVAL, "KMV tabulation node count mismatch");
@@ -626,6 +638,10 @@ int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, i
     }
   }
 
+  if (host_only) {
+    *out = m.release();
+    return 0;
+  }
   // device geometry
   const int NG = d == 2 ? 3 : 6;
   std::vector<float> geo((size_t)NG * E), lgeo((size_t)d * d * (E - m->E0));
@@ -665,6 +681,29 @@ int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, i
     return rc;
   }
   *out = m.release();
+  return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int fwi_mesh_upload(const double* verts, int64_t nverts, const int32_t* cells, int64_t ncells,
+                    const fwi_params* params, fwi_mesh** out) {
+  return mesh_create(verts, nverts, cells, ncells, params, false, out);
+}
+
+int fwi_mesh_prepare_host(const double* verts, int64_t nverts, const int32_t* cells,
+                          int64_t ncells, const fwi_params* params, fwi_mesh** out) {
+  return mesh_create(verts, nverts, cells, ncells, params, true, out);
+}
+
+int fwi_mesh_host_arrays(const fwi_mesh* m, int32_t* conn, double* mass, double* bmass,
+                         double* sigma) {
+  if (!m) return fail(FWI_EINVAL, "null mesh");
+  if (conn) std::memcpy(conn, m->conn.data(), m->conn.size() * sizeof(int32_t));
+  if (mass) std::memcpy(mass, m->M.data(), m->M.size() * sizeof(double));
+  if (bmass) std::memcpy(bmass, m->Mb.data(), m->Mb.size() * sizeof(double));
+  if (sigma) std::memcpy(sigma, m->sigma.data(), m->sigma.size() * sizeof(double));
   return 0;
 }
 
@@ -789,10 +828,11 @@ int fwi_get_dt(const fwi_mesh* m, double* dt) {
 
 int fwi_batch_free(fwi_batch* b) {
   if (!b) return 0;
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   void* ptrs[] = {b->d_inj, b->d_src_elem, b->d_src_phi, b->d_rslot_ptr, b->d_rslot_rec,
                   b->d_rslot_phi, b->d_rec_elem, b->d_rec_phi, b->u, b->v, b->r, b->P, b->Pacc,
                   b->PaccY, b->Y, b->Yacc, b->ua, b->va, b->Pa, b->Ya, b->ckpt, b->ring,
-                  b->gseg, b->gsum, b->gcomp, b->misfit, b->status, b->wav_dev, b->stage_in, b->stage_out,
+                  b->gseg, b->gsum, b->gcomp, b->misfit, b->status, b->wav_dev, b->rec_dev, b->res_dev, b->stage_in, b->stage_out,
                   b->stage_grad};
   for (void* p : ptrs) dfree(p);
   delete b;
@@ -945,9 +985,40 @@ StepArgs base_args(fwi_batch* b) {
 }
 
 void run_step(fwi_batch* b, const StepArgs& a, cudaStream_t st) {
+  cudaEvent_t* e = nullptr;
+  if (b->prof) {
+    while (b->ev.size() < b->ev_used + 3) {
+      cudaEvent_t x;
+      if (cudaEventCreate(&x) != cudaSuccess) break;
+      b->ev.push_back(x);
+    }
+    if (b->ev.size() >= b->ev_used + 3) {
+      e = &b->ev[b->ev_used];
+      b->ev_mode.push_back(a.mode);
+      b->ev_used += 3;
+    }
+  }
+  if (e) cudaEventRecord(e[0], st);
   b->m->ks->launch_step(a, st);
+  if (e) cudaEventRecord(e[1], st);
   fwi::launch_node_update(a, b->m->dim, st);
+  if (e) cudaEventRecord(e[2], st);
   g_launches += 2;
+}
+
+// Adds the recorded event intervals to the batch's totals (the stream must be complete).
+void collect_profile(fwi_batch* b) {
+  for (size_t i = 0; i < b->ev_mode.size(); ++i) {
+    float t1 = 0, t2 = 0;
+    cudaEventElapsedTime(&t1, b->ev[3 * i], b->ev[3 * i + 1]);
+    cudaEventElapsedTime(&t2, b->ev[3 * i + 1], b->ev[3 * i + 2]);
+    const int md = b->ev_mode[i];
+    b->prof_ms[md][0] += t1;
+    b->prof_ms[md][1] += t2;
+    b->prof_steps[md] += 1;
+  }
+  b->ev_mode.clear();
+  b->ev_used = 0;
 }
 
 // state pointers of checkpoint c: u, v, P, Y
@@ -991,6 +1062,7 @@ int check_status(fwi_batch* b, cudaStream_t st) {
   CUDA_TRY(cudaMemcpyAsync(&h, b->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   CUDA_TRY(cudaGetLastError());
+  if (b->prof) collect_profile(b);
   if (h) {
     cudaMemsetAsync(b->status, 0, sizeof(int), st);
     return fail(FWI_ERANGE, "non-finite value in the wavefield (time step above the stability limit?)");
@@ -1033,16 +1105,13 @@ int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* s
   CUDA_TRY(cudaMemcpyAsync(b->wav_dev, wavelet, wn * sizeof(float),
                            is_device_ptr(wavelet) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   const float* wav = b->wav_dev;
-  float* recs = rec_out;
-  const bool host_out = rec_out && !is_device_ptr(rec_out);
-  if (host_out) {
-    if (!b->stage_out && dalloc(&b->stage_out, rn ? rn : 1)) return FWI_ENOMEM;
-    recs = b->stage_out;
-  }
+  const size_t rsz = rn ? rn : 1;
+  if (!b->rec_dev && dalloc(&b->rec_dev, rsz)) return FWI_ENOMEM;
+  float* recs = b->rec_dev;
   if (int rc = zero_state(b, b->u, b->v, b->P, b->Y, st)) return rc;
-  if (recs && rn) CUDA_TRY(cudaMemsetAsync(recs, 0, rn * sizeof(float), st));
+  if (rn) CUDA_TRY(cudaMemsetAsync(recs, 0, rn * sizeof(float), st));
   forward_steps(b, 0, b->nt, wav, recs, true, st);
-  if (recs && b->R) {
+  if (b->R) {
     StepArgs a = base_args(b);
     a.u = b->u;
     a.rec = recs;
@@ -1050,25 +1119,20 @@ int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* s
     b->m->ks->launch_record(a, b->d_rec_elem, b->d_rec_phi, st);
     g_launches += 1;
   }
-  if (host_out && rn) CUDA_TRY(cudaMemcpyAsync(rec_out, recs, rn * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (rec_out && rn)
+    CUDA_TRY(cudaMemcpyAsync(rec_out, recs, rn * sizeof(float),
+                             is_device_ptr(rec_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   if (int rc = check_status(b, st)) return rc;
   b->forward_done = true;
   return 0;
 }
 
-int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream) {
-  if (!b || !residual) return fail(FWI_EINVAL, "fwi_adjoint_shot: null argument");
-  if (!b->forward_done) return fail(FWI_EINVAL, "fwi_adjoint_shot needs a preceding fwi_forward_shot");
-  if (int rc = check_device(b->m)) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+// Adjoint + gradient accumulation for a device residual [S][nt+1][R].
+int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
   const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
-  const float* res = residual;
-  if (!is_device_ptr(residual)) {
-    const size_t wn = (size_t)b->S * b->nt;
-    if (!b->stage_in && dalloc(&b->stage_in, std::max(wn, rn))) return FWI_ENOMEM;
-    CUDA_TRY(cudaMemcpyAsync(b->stage_in, residual, rn * sizeof(float), cudaMemcpyHostToDevice, st));
-    res = b->stage_in;
-  }
   fwi::launch_misfit(res, (int64_t)rn, b->misfit, st);
   g_launches += 1;
   StepArgs a = base_args(b);
@@ -1107,6 +1171,45 @@ int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream) {
   return check_status(b, st);
 }
 
+int stage_signal(fwi_batch* b, const float* src, size_t count, const float** dev, cudaStream_t st) {
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return 0;
+  }
+  const size_t rn = (size_t)b->S * (b->nt + 1) * b->R, wn = (size_t)b->S * b->nt;
+  if (!b->stage_in && dalloc(&b->stage_in, std::max(std::max(wn, rn), (size_t)1))) return FWI_ENOMEM;
+  CUDA_TRY(cudaMemcpyAsync(b->stage_in, src, count * sizeof(float), cudaMemcpyHostToDevice, st));
+  *dev = b->stage_in;
+  return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream) {
+  if (!b || !residual) return fail(FWI_EINVAL, "fwi_adjoint_shot: null argument");
+  if (!b->forward_done) return fail(FWI_EINVAL, "fwi_adjoint_shot needs a preceding fwi_forward_shot");
+  if (int rc = check_device(b->m)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* res = nullptr;
+  if (int rc = stage_signal(b, residual, (size_t)b->S * (b->nt + 1) * b->R, &res, st)) return rc;
+  return adjoint_device(b, res, st);
+}
+
+int fwi_adjoint_misfit(fwi_batch* b, const float* observed, void* stream) {
+  if (!b || !observed) return fail(FWI_EINVAL, "fwi_adjoint_misfit: null argument");
+  if (!b->forward_done) return fail(FWI_EINVAL, "fwi_adjoint_misfit needs a preceding fwi_forward_shot");
+  if (int rc = check_device(b->m)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
+  const float* obs = nullptr;
+  if (int rc = stage_signal(b, observed, rn, &obs, st)) return rc;
+  if (!b->res_dev && dalloc(&b->res_dev, rn ? rn : 1)) return FWI_ENOMEM;
+  fwi::launch_residual(b->rec_dev, obs, b->res_dev, (int64_t)rn, st);
+  g_launches += 1;
+  return adjoint_device(b, b->res_dev, st);
+}
+
 int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream) {
   if (!b || !grad_out) return fail(FWI_EINVAL, "fwi_gradient: null argument");
   if (int rc = check_device(b->m)) return rc;
@@ -1129,6 +1232,24 @@ int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* strea
   CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, (size_t)N * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(b->misfit, 0, sizeof(double), st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int fwi_profile(fwi_batch* b, int enable) {
+  if (!b) return fail(FWI_EINVAL, "null batch");
+  b->prof = enable != 0;
+  return 0;
+}
+
+int fwi_profile_read(fwi_batch* b, double* ms, int64_t* steps) {
+  if (!b || !ms || !steps) return fail(FWI_EINVAL, "null argument");
+  for (int md = 0; md < 2; ++md) {
+    ms[2 * md] = b->prof_ms[md][0];
+    ms[2 * md + 1] = b->prof_ms[md][1];
+    steps[md] = b->prof_steps[md];
+    b->prof_ms[md][0] = b->prof_ms[md][1] = 0;
+    b->prof_steps[md] = 0;
+  }
   return 0;
 }
 

@@ -84,5 +84,6 @@ void launch_finish_gradient(const double* gsum, const double* gcomp, const float
                             const double* M, const unsigned char* mask, double* out, int64_t N,
                             cudaStream_t st);
 void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st);
+void launch_residual(const float* d, const float* obs, float* res, int64_t n, cudaStream_t st);
 
 }  // namespace fwi

@@ -88,6 +88,17 @@ __global__ void misfit_kernel(const float* __restrict__ r, int64_t n, double* ac
   if (threadIdx.x == 0) atomicAdd(acc, 0.5 * part[0]);
 }
 
+__global__ void residual_kernel(const float* __restrict__ d, const float* __restrict__ obs,
+                                float* __restrict__ res, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) res[i] = d[i] - obs[i];
+}
+
+void launch_residual(const float* d, const float* obs, float* res, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, obs, res, n);
+}
+
 void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st) {
   if (n == 0) return;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 1216);

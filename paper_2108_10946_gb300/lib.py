@@ -50,6 +50,8 @@ def load():
     lib = ctypes.CDLL(path)
     sig = {
         "fwi_mesh_upload": (ctypes.c_int, [_P, _I64, _P, _I64, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+        "fwi_mesh_prepare_host": (ctypes.c_int, [_P, _I64, _P, _I64, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+        "fwi_mesh_host_arrays": (ctypes.c_int, [_P, _P, _P, _P, _P]),
         "fwi_num_dofs": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
         "fwi_dof_coords": (ctypes.c_int, [_P, _P]),
         "fwi_element": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P, _P]),
@@ -60,8 +62,11 @@ def load():
         "fwi_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
         "fwi_forward_shot": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_adjoint_shot": (ctypes.c_int, [_P, _P, _P]),
+        "fwi_adjoint_misfit": (ctypes.c_int, [_P, _P, _P]),
         "fwi_gradient": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_batch_free": (ctypes.c_int, [_P]),
+        "fwi_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+        "fwi_profile_read": (ctypes.c_int, [_P, _P, _P]),
         "fwi_mesh_free": (ctypes.c_int, [_P]),
         "fwi_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
         "fwi_launch_count": (ctypes.c_int64, []),
@@ -130,7 +135,8 @@ class Mesh:
     """A mesh resident on the current CUDA device (fwi_mesh_upload)."""
 
     def __init__(self, verts, cells, k, nsteps, dt=0.0, cfl_factor=0.9, box=None, layer_faces=0,
-                 layer_width=0.0, sigma_max=0.0, absorbing=False, ckpt_stride=50, water_speed=0.0):
+                 layer_width=0.0, sigma_max=0.0, absorbing=False, ckpt_stride=50, water_speed=0.0,
+                 host_only=False):
         lib = load()
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -153,8 +159,10 @@ class Mesh:
         self.params = p
         self.dim = p.dim
         h = ctypes.c_void_p()
-        _check(lib.fwi_mesh_upload(_ptr(verts), verts.shape[0], _ptr(cells), cells.shape[0],
-                                   ctypes.byref(p), ctypes.byref(h)))
+        fn = lib.fwi_mesh_prepare_host if host_only else lib.fwi_mesh_upload
+        _check(fn(_ptr(verts), verts.shape[0], _ptr(cells), cells.shape[0], ctypes.byref(p),
+                  ctypes.byref(h)))
+        self.E = cells.shape[0]
         self._h = h
         n = ctypes.c_int64()
         _check(lib.fwi_num_dofs(h, ctypes.byref(n)))
@@ -174,6 +182,17 @@ class Mesh:
         dh = np.zeros((self.dim, nn, nn))
         _check(_lib.fwi_element(self._h, ctypes.byref(n), _ptr(xh), _ptr(w), _ptr(dh)))
         return xh, w, dh
+
+    def host_arrays(self):
+        """(conn [E][n], mass [N], boundary mass [N], sigma [N][dim]) as prepared on the host."""
+        xh, _, _ = self.element()
+        n = xh.shape[0]
+        conn = np.zeros((self.E, n), dtype=np.int32)
+        M = np.zeros(self.N)
+        Mb = np.zeros(self.N)
+        sig = np.zeros((self.N, self.dim))
+        _check(_lib.fwi_mesh_host_arrays(self._h, _ptr(conn), _ptr(M), _ptr(Mb), _ptr(sig)))
+        return conn, M, Mb, sig
 
     def set_velocity(self, c):
         c = np.ascontiguousarray(c, dtype=np.float64)
@@ -224,11 +243,27 @@ class Batch:
         """residual [S][Nt+1][R] float32 = d - dtilde (host or device)."""
         _check(_lib.fwi_adjoint_shot(self._h, _ptr(residual), _stream_ptr(stream)))
 
+    def adjoint_misfit(self, observed, stream=None):
+        """observed [S][Nt+1][R] float32 (host or device); residual formed on the device."""
+        _check(_lib.fwi_adjoint_misfit(self._h, _ptr(observed), _stream_ptr(stream)))
+
     def gradient(self, out, stream=None):
         """out [N] float64 (host or device); returns the misfit J."""
         J = ctypes.c_double()
         _check(_lib.fwi_gradient(self._h, _ptr(out), ctypes.byref(J), _stream_ptr(stream)))
         return J.value
+
+    def profile(self, enable=True):
+        _check(_lib.fwi_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{'fwd_elem_ms', 'fwd_node_ms', 'adj_elem_ms', 'adj_node_ms', 'fwd_steps',
+        'adj_steps'} since the last read."""
+        ms = np.zeros(4)
+        steps = np.zeros(2, dtype=np.int64)
+        _check(_lib.fwi_profile_read(self._h, _ptr(ms), _ptr(steps)))
+        return dict(fwd_elem_ms=ms[0], fwd_node_ms=ms[1], adj_elem_ms=ms[2], adj_node_ms=ms[3],
+                    fwd_steps=int(steps[0]), adj_steps=int(steps[1]))
 
     def close(self):
         if getattr(self, "_h", None):
