@@ -220,6 +220,13 @@ def _orbit_points_param(kind, p):
     return np.array([g[list(pp)] for pp in _orbit_fixed_perms(kind)])
 
 
+def _split_kind(kind):
+    """'e' -> ('e', None) free edge pair; ('e', t) -> edge pair held fixed at t."""
+    if isinstance(kind, tuple):
+        return kind[0], np.array(kind[1:], dtype=np.float64)
+    return kind, None
+
+
 def _moment_residual_jac(kinds, x, D):
     monos = _monomials(2, D)
     exact = np.array([simplex_monomial_integral(e) for e in monos])
@@ -227,11 +234,11 @@ def _moment_residual_jac(kinds, x, D):
     J = np.zeros((len(monos), len(x)))
     k = 0
     for kind in kinds:
-        npar = _NPAR[kind]
-        p = x[k:k + npar]
+        kind, fixed = _split_kind(kind)
+        npar = 0 if fixed is not None else _NPAR[kind]
+        p = fixed if fixed is not None else x[k:k + npar]
         w = x[k + npar]
-        B = _orbit_points_param(kind, p)
-        X = bary_to_ref(B)
+        X = bary_to_ref(_orbit_points_param(kind, p))
         for r_i, e in enumerate(monos):
             m = _mono(e)
             vals = peval(m, X)
@@ -239,26 +246,27 @@ def _moment_residual_jac(kinds, x, D):
             J[r_i, k + npar] = vals.sum()
             if npar:
                 g = pgrad(m, X)  # (npts, 2)
-                # d(point)/d(param) by central differences of the generator (exact: linear)
                 for j in range(npar):
                     dp = np.zeros(npar)
                     dp[j] = 1.0
-                    dX = bary_to_ref(_orbit_points_param(kind, p + dp)) - bary_to_ref(
-                        _orbit_points_param(kind, p))
+                    # the orbit points are affine in the parameters: exact difference
+                    dX = bary_to_ref(_orbit_points_param(kind, p + dp)) - X
                     J[r_i, k + j] = w * np.sum(g * dX)
         k += npar + 1
     return r, J
 
 
 def newton_orbit_rule(kinds, params0, D, iters=60):
-    """Gauss-Newton on the moment equations over orbit parameters and weights. Initial
-    weights come from a linear least-squares solve at the starting positions."""
-    # starting weights
+    """Gauss-Newton on the moment equations over the free orbit parameters and all
+    weights. A kind given as a tuple (kind, value) is an orbit held at a fixed position.
+    Initial weights come from a linear least-squares solve at the starting positions."""
     pts, lab = [], []
     k = 0
     for i, kind in enumerate(kinds):
-        npar = _NPAR[kind]
-        B = _orbit_points_param(kind, np.array(params0[k:k + npar]))
+        kd, fixed = _split_kind(kind)
+        npar = 0 if fixed is not None else _NPAR[kd]
+        p = fixed if fixed is not None else np.array(params0[k:k + npar])
+        B = _orbit_points_param(kd, p)
         pts.append(bary_to_ref(B))
         lab += [i] * len(B)
         k += npar
@@ -275,7 +283,8 @@ def newton_orbit_rule(kinds, params0, D, iters=60):
     x = []
     k = 0
     for i, kind in enumerate(kinds):
-        npar = _NPAR[kind]
+        kd, fixed = _split_kind(kind)
+        npar = 0 if fixed is not None else _NPAR[kd]
         x += list(params0[k:k + npar]) + [w0[i]]
         k += npar
     x = np.array(x, dtype=np.float64)
@@ -289,23 +298,29 @@ def newton_orbit_rule(kinds, params0, D, iters=60):
     return x, float(np.max(np.abs(r)))
 
 
-# Coarse starting points (two significant digits) for the Newton solve; orbit structure
-# (a reading: the paper does not list these elements' nodes):
-#   KMV4tri: vertices, edge midpoints, one edge pair, two interior 3-orbits; exact to 7.
-#   KMV5tri: see _KMV5_KINDS; exact to degree 10.
+# Coarse starting points (two significant digits) for the Newton solves; orbit structures
+# are readings (the paper does not list these elements' nodes):
+#   KMV4tri: vertices, edge midpoints, one edge pair, two interior 3-orbits; the degree-7
+#     equations have a unique solution.
+#   KMV5tri: vertices, two edge pairs, three interior 3-orbits, one interior 6-orbit. No
+#     positive degree-10 rule of this structure was found by multistart search; the
+#     degree-9 (= 2k - 1) equations leave a two-parameter family, fixed here by placing the
+#     edge pairs at t = 0.19 and t = 0.32 (two-digit values near the member of the family
+#     closest to degree-10 exactness); the interior positions and all weights then follow
+#     from the twelve degree-9 equations.
 _KMV4_KINDS = ["v", "m", "e", "3", "3"]
 _KMV4_START = [0.21, 0.42, 0.13]
-_KMV5_KINDS = None  # filled below
-_KMV5_START = None
+_KMV4_DEGREE = 7
+_KMV5_KINDS = ["v", ("e", 0.19), ("e", 0.32), "3", "3", "3", "6"]
+_KMV5_START = [0.07, 0.48, 0.39, 0.63, 0.27]
+_KMV5_DEGREE = 9
 
 
 def _solved_tri_nodes(k):
     if k == 4:
-        kinds, start, D = _KMV4_KINDS, _KMV4_START, 7
-    elif k == 5 and _KMV5_KINDS is None:
-        raise NotImplementedError("KMV5tri nodes are not settled")
+        kinds, start, D = _KMV4_KINDS, _KMV4_START, _KMV4_DEGREE
     elif k == 5:
-        kinds, start, D = _KMV5_KINDS, _KMV5_START, 10
+        kinds, start, D = _KMV5_KINDS, _KMV5_START, _KMV5_DEGREE
     else:
         raise ValueError(k)
     x, res = newton_orbit_rule(kinds, start, D)
@@ -314,8 +329,9 @@ def _solved_tri_nodes(k):
     gens = []
     kk = 0
     for kind in kinds:
-        npar = _NPAR[kind]
-        gens.append(_gen(kind, x[kk:kk + npar]))
+        kd, fixed = _split_kind(kind)
+        npar = 0 if fixed is not None else _NPAR[kd]
+        gens.append(_gen(kd, fixed if fixed is not None else x[kk:kk + npar]))
         kk += npar + 1
     return gens
 

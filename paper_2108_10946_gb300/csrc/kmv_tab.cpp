@@ -281,13 +281,15 @@ bool orbit_weights(const std::vector<std::vector<Bary>>& orbits, int dim,
 // kinds: 'v' vertex, 'm' edge midpoint, 'e' edge pair (t,1-t,0), '3' (a,a,1-2a),
 // '6' (a,b,1-a-b). Unknowns: the orbit parameters and one weight per orbit.
 
+// 'E' is an edge pair held at a fixed position (taken from the fixed list, in order)
 int npar(char c) { return c == 'e' || c == '3' ? 1 : (c == '6' ? 2 : 0); }
 
 Bary gen_of(char c, const ld* p) {
   switch (c) {
     case 'v': return {1, 0, 0};
     case 'm': return {0.5L, 0.5L, 0};
-    case 'e': return {p[0], 1 - p[0], 0};
+    case 'e':
+    case 'E': return {p[0], 1 - p[0], 0};
     case '3': return {p[0], p[0], 1 - 2 * p[0]};
     default: return {p[0], p[1], 1 - p[0] - p[1]};
   }
@@ -300,20 +302,21 @@ std::vector<std::array<int, 3>> perms_of(char c) {
   return {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 }
 
-void residual_jacobian(const std::string& kinds, const std::vector<ld>& x, int D,
-                       std::vector<ld>& r, std::vector<ld>& J, int& rows) {
+void residual_jacobian(const std::string& kinds, const std::vector<ld>& fixed,
+                       const std::vector<ld>& x, int D, std::vector<ld>& r, std::vector<ld>& J,
+                       int& rows) {
   auto ex = exps_up_to(2, D);
   rows = (int)ex.size();
   int nx = (int)x.size();
   r.assign(rows, 0);
   J.assign(rows * nx, 0);
   for (int i = 0; i < rows; ++i) r[i] = -mono_integral(ex[i].data(), 2);
-  int k = 0;
+  int k = 0, fi = 0;
   for (char c : kinds) {
     int np = npar(c);
     ld w = x[k + np];
-    Bary g = gen_of(c, x.data() + k);
-    std::vector<Bary> dg;  // derivative of the generator w.r.t. each parameter
+    Bary g = c == 'E' ? gen_of(c, &fixed[fi++]) : gen_of(c, x.data() + k);
+    std::vector<Bary> dg;  // derivative of the generator w.r.t. each free parameter
     if (c == 'e') dg = {{1, -1, 0}};
     if (c == '3') dg = {{1, 1, -2}};
     if (c == '6') dg = {{1, 0, -1}, {0, 1, -1}};
@@ -336,17 +339,20 @@ void residual_jacobian(const std::string& kinds, const std::vector<ld>& x, int D
   }
 }
 
-bool solve_orbits(const std::string& kinds, const std::vector<ld>& start_params, int D,
-                  std::vector<Bary>& gens, std::string& err) {
+bool solve_orbits(const std::string& kinds, const std::vector<ld>& fixed,
+                  const std::vector<ld>& start_params, int D, std::vector<Bary>& gens,
+                  std::string& err) {
   // starting weights from the linear moment equations at the starting positions
-  std::vector<std::vector<Bary>> orbits;
+  std::vector<Bary> gen0;
   {
-    int k = 0;
+    int k = 0, fi = 0;
     for (char c : kinds) {
-      orbits.push_back(orbit_of(gen_of(c, start_params.data() + k)));
+      gen0.push_back(c == 'E' ? gen_of(c, &fixed[fi++]) : gen_of(c, start_params.data() + k));
       k += npar(c);
     }
   }
+  std::vector<std::vector<Bary>> orbits;
+  for (auto& g : gen0) orbits.push_back(orbit_of(g));
   Moments M0 = moment_system(orbits, 2, D, {});
   std::vector<ld> w0;
   lstsq(M0.A, M0.b, M0.rows, (int)kinds.size(), w0);
@@ -362,7 +368,7 @@ bool solve_orbits(const std::string& kinds, const std::vector<ld>& start_params,
   std::vector<ld> r, J;
   int rows = 0;
   for (int it = 0; it < 100; ++it) {
-    residual_jacobian(kinds, x, D, r, J, rows);
+    residual_jacobian(kinds, fixed, x, D, r, J, rows);
     std::vector<ld> step;
     if (!lstsq(J, r, rows, (int)x.size(), step)) break;
     ld mx = 0;
@@ -372,7 +378,7 @@ bool solve_orbits(const std::string& kinds, const std::vector<ld>& start_params,
     }
     if (mx < 1e-18L) break;
   }
-  residual_jacobian(kinds, x, D, r, J, rows);
+  residual_jacobian(kinds, fixed, x, D, r, J, rows);
   ld res = 0;
   for (ld v : r) res = std::max(res, std::fabs(v));
   if (res > 1e-15L) {
@@ -380,9 +386,9 @@ bool solve_orbits(const std::string& kinds, const std::vector<ld>& start_params,
     return false;
   }
   gens.clear();
-  int k = 0;
+  int k = 0, fi = 0;
   for (char c : kinds) {
-    gens.push_back(gen_of(c, x.data() + k));
+    gens.push_back(c == 'E' ? gen_of(c, &fixed[fi++]) : gen_of(c, x.data() + k));
     k += npar(c) + 1;
   }
   return true;
@@ -413,10 +419,14 @@ bool build(int dim, int k, Element& el, std::string& err) {
       gens = {{1, 0, 0}, {t, 1 - t, 0}, {a, a, 1 - 2 * a}};
     } else if (k == 4) {
       // vertices, edge midpoints, one edge pair, two interior (a,a,1-2a) orbits; exact to 7
-      if (!solve_orbits("vme33", {0.212L, 0.425L, 0.131L}, 7, gens, err)) return false;
+      if (!solve_orbits("vme33", {}, {0.212L, 0.425L, 0.131L}, 7, gens, err)) return false;
     } else if (k == 5) {
-      err = "KMV5tri is not available";
-      return false;
+      // vertices, edge pairs held at t = 0.19 and 0.32, three interior (a,a,1-2a) orbits and
+      // one (a,b,1-a-b) orbit; interior positions and weights from the degree-9 (= 2k-1)
+      // moment equations (no positive degree-10 rule of this structure is known here)
+      if (!solve_orbits("vEE3336", {0.19L, 0.32L}, {0.072L, 0.485L, 0.393L, 0.629L, 0.267L}, 9,
+                        gens, err))
+        return false;
     } else {
       err = "KMV triangles are available for k = 2..5";
       return false;

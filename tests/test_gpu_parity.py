@@ -82,7 +82,7 @@ def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=mode
     return out
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_forward_records_2d(lib, k):
     V, C, lay = _case2d(k)
     srcs = [[0.5, 0.3], [0.31, 0.62]]
@@ -94,7 +94,7 @@ def test_forward_records_2d(lib, k):
         assert err < REC_TOL
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_forward_and_gradient_2d_layer(lib, k):
     V, C, lay = _case2d(k, n=12, layer=True)
     srcs = [[0.5, 0.1], [0.2, 0.15]]
@@ -119,3 +119,25 @@ def test_gershgorin_dt_matches_oracle(lib):
     mesh.set_velocity(models.smooth2d(xg))
     orc = OracleCase(V, C, 3, models.smooth2d, 1.0, 1)
     assert abs(mesh.dt - 0.8 * orc.ops.cfl_dt()) < 1e-12 * mesh.dt
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_forward_and_gradient_3d_layer(lib, k):
+    """KMV2tet / KMV3tet with the 3D damping layer (u, p in R^3, omega) and the absorbing
+    boundary: records and gradient against the oracle."""
+    g = np.linspace(0.0, 1.0, 6)
+    gz = np.linspace(0.0, 0.8, 5)
+    V, C = meshes.kuhn_tets(g, g, gz)
+    lay = dict(box=[(0.2, 0.8), (0.2, 0.8), (-10.0, 0.6)], faces=0b101111, width=0.2,
+               smax=signals.sigma_max(2.2, 0.2))
+    srcs = [[0.5, 0.5, 0.1], [0.4, 0.55, 0.15]]
+    recs = [[x, y, 0.5] for x in (0.3, 0.5, 0.7) for y in (0.35, 0.65)]
+    o = _run_both(lib, V, C, k, lay, 0.5, srcs, recs, absorbing=True, grad=True,
+                  cfun=models.smooth3d, f=6.0)
+    for s in range(2):
+        err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
+        print(f"3D k={k} shot {s}: records rel-L2 = {err:.3e}")
+        assert err < REC_TOL
+    gerr = rel_l2(o["G_gpu"], o["G_orc"])
+    print(f"3D k={k}: gradient rel-L2 = {gerr:.3e}")
+    assert gerr < GRAD_TOL

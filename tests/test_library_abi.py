@@ -37,7 +37,7 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
         L.load()
 
 
-@pytest.mark.parametrize("dim,k", [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3)])
+@pytest.mark.parametrize("dim,k", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3)])
 def test_library_tabulation_matches_oracle(dim, k):
     """The library's C++ KMV tabulation and the oracle's are independent implementations of
     the same element: nodes (as a set), weights and derivative matrices must agree."""

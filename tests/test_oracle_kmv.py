@@ -13,7 +13,7 @@ from oracle import mesh as om
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
-TRI = [2, 3, 4]
+TRI = [2, 3, 4, 5]
 TET = [2, 3]
 
 
@@ -69,7 +69,7 @@ def test_paper_tet_nodes_are_used():
         assert round(v, 12) in params
 
 
-@pytest.mark.parametrize("dim,k,degree", [(2, 2, 3), (2, 3, 5), (2, 4, 7),
+@pytest.mark.parametrize("dim,k,degree", [(2, 2, 3), (2, 3, 5), (2, 4, 7), (2, 5, 9),
                                           (3, 2, 3), (3, 3, 5)])
 def test_exactness_degree_and_positivity(dim, k, degree):
     """Brute force: integrate every monomial up to the degree with the rule and compare

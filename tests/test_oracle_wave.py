@@ -43,7 +43,7 @@ def test_ricker_closed_form_and_input_signal():
     assert np.allclose(s, analytic.ricker(np.arange(500) * dt, f), atol=1e-7)
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_discrete_energy_is_conserved(k):
     m = _sq_mesh(k, 6)
     c = np.random.default_rng(0).uniform(1.5, 3.0, m.N)
@@ -97,7 +97,7 @@ def _dot_test(ops, m, nt, src, recs):
     return abs(lhs - rhs) / abs(lhs)
 
 
-@pytest.mark.parametrize("k,layer", [(2, False), (3, True), (4, True)])
+@pytest.mark.parametrize("k,layer", [(2, False), (3, True), (5, True)])
 def test_adjoint_dot_product_2d(k, layer):
     m = _sq_mesh(k, 8, L=1.5, x0=-0.25)
     c = np.random.default_rng(2).uniform(1.5, 2.5, m.N)
