@@ -60,6 +60,9 @@ typedef struct fwi_batch fwi_batch;
  *   ckpt_stride      forward checkpoint spacing in steps for the adjoint's recompute.
  *   water_speed      the gradient is zeroed where c < water_speed (Section 5.4: 1.51
  *                    km/s) and inside the damping layer; <= 0 disables the speed test.
+ *   layout           0: chunked (elements grouped in chunks that assemble in shared memory;
+ *                    the default), 1: plain (one thread per element and shot scattering
+ *                    with global atomics; the unfused reference form).
  */
 typedef struct {
   int dim;
@@ -75,6 +78,7 @@ typedef struct {
   int absorbing;
   int ckpt_stride;
   double water_speed;
+  int layout;
 } fwi_params;
 
 /* Builds the DoF numbering, locality order and per-element geometry of a simplex mesh

@@ -110,6 +110,14 @@ struct fwi_mesh {
   const fwi::KernelSet* ks = nullptr;
   int64_t nverts = 0;
   int E = 0, E0 = 0, N = 0, Ns = 0, Nl = 0;
+  int layout = 0;     // 0 chunked (shared-memory assembly), 1 plain (global atomics)
+  int P = 32;         // elements per chunk
+  int N_own = 0;      // DoFs owned by one chunk: [0, N_own); halo DoFs [N_own, N)
+  int L_max = 0;      // largest local DoF table of a chunk (owned + halo)
+  std::vector<int32_t> bub;                       // [E] first bubble DoF of every element
+  std::vector<int32_t> ch_e0, ch_own_lo, ch_nsh;  // chunk element ranges, owned ranges
+  std::vector<int32_t> ch_halo_ptr, halo_ids;     // per-chunk halo lists (global DoF ids)
+  std::vector<uint16_t> lconn;                    // [ns][E] chunk-local index of shared nodes
   std::vector<double> verts;
   std::vector<int32_t> cells;      // user order
   std::vector<int32_t> order;      // new element -> user element
@@ -133,6 +141,11 @@ struct fwi_mesh {
   float* d_lcf = nullptr;    // [Nl][count]
   double* d_M = nullptr;
   unsigned char* d_mask = nullptr;
+  int* d_bub = nullptr;
+  int* d_chunks = nullptr;   // [nch][6]: e0, ne, own_lo, own_n, nsh, halo_ptr
+  int* d_halo = nullptr;     // halo DoF ids, chunk by chunk
+  unsigned short* d_lconn = nullptr;
+  int nch() const { return (int)ch_e0.size() - 1; }
 };
 
 struct fwi_batch {
@@ -168,6 +181,7 @@ struct fwi_batch {
   float* stage_out = nullptr;
   double* stage_grad = nullptr;
   bool forward_done = false;
+  int launch_error = 0;  // first kernel configuration error of a call (cudaError_t)
   // optional per-kernel timing with CUDA events (fwi_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -355,13 +369,14 @@ double gershgorin(const fwi_mesh* m) {
       }
     }
   };
-  // incidence of shared DoFs
-  std::vector<int64_t> ptr(m->Ns + 1, 0);
+  // incidence (element, local node) of every shared DoF, CSR over all DoFs
+  const int N = m->N;
+  std::vector<int64_t> ptr(N + 1, 0);
   for (int e = 0; e < E; ++e)
     for (int a = 0; a < m->ns; ++a) ptr[m->conn[(size_t)e * n + a] + 1]++;
-  for (int i = 0; i < m->Ns; ++i) ptr[i + 1] += ptr[i];
+  for (int i = 0; i < N; ++i) ptr[i + 1] += ptr[i];
   std::vector<int64_t> fillp(ptr.begin(), ptr.end() - 1);
-  std::vector<int32_t> inc((size_t)ptr[m->Ns] * 2);
+  std::vector<int32_t> inc((size_t)ptr[N] * 2);
   for (int e = 0; e < E; ++e)
     for (int a = 0; a < m->ns; ++a) {
       int i = m->conn[(size_t)e * n + a];
@@ -375,11 +390,12 @@ double gershgorin(const fwi_mesh* m) {
     while (v > cur && !best.compare_exchange_weak(cur, v)) {
     }
   };
-  parallel_for(m->Ns, [&](int64_t i0, int64_t i1) {
+  parallel_for(N, [&](int64_t i0, int64_t i1) {
     std::vector<double> rw(n);
     std::vector<std::pair<int, double>> acc;
     double loc = 0;
     for (int64_t i = i0; i < i1; ++i) {
+      if (ptr[i] == ptr[i + 1]) continue;  // bubble DoF: handled element by element below
       acc.clear();
       for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
         int e = inc[t * 2], a = inc[t * 2 + 1];
@@ -451,6 +467,8 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
   m->dim = d;
   m->k = params->k;
   m->ks = ks;
+  m->layout = params->layout == 1 ? 1 : 0;
+  m->P = d == 2 ? 32 : 16;
   if (!host_only) CUDA_TRY(cudaGetDevice(&m->device));
   std::string err;
   if (!kmvtab::build(d, params->k, m->el, err)) return fail(FWI_EINVAL, "KMV tabulation: " + err);
@@ -552,11 +570,94 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
       m->conn[(size_t)e * n + q] = it->second;
     }
   }
-  m->Ns = next;
-  if ((int64_t)m->Ns + (int64_t)E * m->ni > INT32_MAX) return fail(FWI_EINVAL, "too many DoFs");
-  m->N = m->Ns + E * m->ni;
+  const int nprov = next;
+  if ((int64_t)nprov + (int64_t)E * m->ni > INT32_MAX) return fail(FWI_EINVAL, "too many DoFs");
+  m->bub.assign(E, 0);
+  if (m->layout == 1) {
+    // plain layout: shared DoFs by first touch, then the bubble DoFs element by element
+    m->Ns = nprov;
+    m->N = m->Ns + E * m->ni;
+    for (int e = 0; e < E; ++e) m->bub[e] = m->Ns + e * m->ni;
+  } else {
+    // chunked layout: chunks of P consecutive elements (never straddling E0); a shared DoF
+    // touched by one chunk only is owned by it; each chunk's owned shared DoFs and its
+    // elements' bubble DoFs form one contiguous range; DoFs shared by several chunks
+    // (the halo) are numbered last
+    const int P = m->P;
+    m->ch_e0.clear();
+    for (int e = 0; e < m->E0; e += P) m->ch_e0.push_back(e);
+    for (int e = m->E0; e < E; e += P) m->ch_e0.push_back(e);
+    m->ch_e0.push_back(E);
+    const int nch = (int)m->ch_e0.size() - 1;
+    std::vector<int> first(nprov, -1);
+    std::vector<char> halo(nprov, 0);
+    for (int c = 0; c < nch; ++c)
+      for (int e = m->ch_e0[c]; e < m->ch_e0[c + 1]; ++e)
+        for (int q = 0; q < m->ns; ++q) {
+          int pid = m->conn[(size_t)e * n + q];
+          if (first[pid] < 0) first[pid] = c;
+          else if (first[pid] != c) halo[pid] = 1;
+        }
+    std::vector<int32_t> fin(nprov, -1);
+    m->ch_own_lo.assign(nch + 1, 0);
+    m->ch_nsh.assign(nch, 0);
+    int32_t cur = 0;
+    for (int c = 0; c < nch; ++c) {
+      m->ch_own_lo[c] = cur;
+      for (int e = m->ch_e0[c]; e < m->ch_e0[c + 1]; ++e)
+        for (int q = 0; q < m->ns; ++q) {
+          int pid = m->conn[(size_t)e * n + q];
+          if (!halo[pid] && fin[pid] < 0) fin[pid] = cur++;
+        }
+      m->ch_nsh[c] = cur - m->ch_own_lo[c];
+      for (int e = m->ch_e0[c]; e < m->ch_e0[c + 1]; ++e) {
+        m->bub[e] = cur;
+        cur += m->ni;
+      }
+    }
+    m->ch_own_lo[nch] = cur;
+    m->N_own = cur;
+    for (int e = 0; e < E; ++e)
+      for (int q = 0; q < m->ns; ++q) {
+        int pid = m->conn[(size_t)e * n + q];
+        if (fin[pid] < 0) fin[pid] = cur++;
+      }
+    m->N = cur;
+    m->Ns = nprov;  // number of shared DoFs (owned + halo)
+    for (int e = 0; e < E; ++e)
+      for (int q = 0; q < m->ns; ++q) m->conn[(size_t)e * n + q] = fin[m->conn[(size_t)e * n + q]];
+    // per-chunk halo lists and local connectivity
+    m->ch_halo_ptr.assign(nch + 1, 0);
+    m->halo_ids.clear();
+    m->lconn.assign((size_t)m->ns * E, 0);
+    m->L_max = 0;
+    std::unordered_map<int32_t, int> hmap;
+    for (int c = 0; c < nch; ++c) {
+      hmap.clear();
+      const int own_lo = m->ch_own_lo[c], own_n = m->ch_own_lo[c + 1] - own_lo;
+      for (int e = m->ch_e0[c]; e < m->ch_e0[c + 1]; ++e)
+        for (int q = 0; q < m->ns; ++q) {
+          int dof = m->conn[(size_t)e * n + q];
+          int loc;
+          if (dof < m->N_own) {
+            loc = dof - own_lo;
+          } else {
+            auto it = hmap.find(dof);
+            if (it == hmap.end()) {
+              it = hmap.emplace(dof, (int)hmap.size()).first;
+              m->halo_ids.push_back(dof);
+            }
+            loc = own_n + it->second;
+          }
+          if (loc < 0 || loc > 65535) return fail(FWI_EINVAL, "chunk too large for 16-bit local indices");
+          m->lconn[(size_t)q * E + e] = (uint16_t)loc;
+        }
+      m->ch_halo_ptr[c + 1] = (int)m->halo_ids.size();
+      m->L_max = std::max(m->L_max, own_n + (int)hmap.size());
+    }
+  }
   for (int e = 0; e < E; ++e)
-    for (int j = 0; j < m->ni; ++j) m->conn[(size_t)e * n + m->ns + j] = m->Ns + e * m->ni + j;
+    for (int j = 0; j < m->ni; ++j) m->conn[(size_t)e * n + m->ns + j] = m->bub[e] + j;
   const int N = m->N;
 
   // DoF coordinates, lumped mass, damping profile
@@ -579,16 +680,20 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
     }
   }
   m->sigma.assign((size_t)N * d, 0);
+  // Layer auxiliaries (P, and omega in 3D) are stored for every DoF of a layer element:
+  // omega is a field on the whole mesh (omega_t = u), and the lumped gradient of omega at a
+  // layer node takes its values at the element's other nodes, damped or not. Outside the
+  // layer elements no term reads P or omega.
   m->pidx.assign(N, -1);
   m->Nl = 0;
-  for (int i = 0; i < N; ++i) {
-    bool any = false;
-    for (int c = 0; c < d; ++c) {
+  for (int i = 0; i < N; ++i)
+    for (int c = 0; c < d; ++c)
       m->sigma[(size_t)i * d + c] = sigma_at(m->p, d, &m->dof_xyz[(size_t)i * d], c);
-      any |= m->sigma[(size_t)i * d + c] > 0;
+  for (int e = m->E0; e < E; ++e)
+    for (int q = 0; q < n; ++q) {
+      const int i = m->conn[(size_t)e * n + q];
+      if (m->pidx[i] < 0) m->pidx[i] = m->Nl++;
     }
-    if (any) m->pidx[i] = m->Nl++;
-  }
   // lumped boundary mass: facets owned by one element
   m->Mb.assign(N, 0);
   if (m->p.absorbing) {
@@ -669,7 +774,35 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
   std::vector<int> conn_dev((size_t)m->ns * E);
   for (int e = 0; e < E; ++e)
     for (int q = 0; q < m->ns; ++q) conn_dev[(size_t)q * E + e] = m->conn[(size_t)e * n + q];
+  std::vector<int> chunks;
+  if (m->layout == 0) {
+    for (int c = 0; c < m->nch(); ++c) {
+      chunks.push_back(m->ch_e0[c]);
+      chunks.push_back(m->ch_e0[c + 1] - m->ch_e0[c]);
+      chunks.push_back(m->ch_own_lo[c]);
+      chunks.push_back(m->ch_own_lo[c + 1] - m->ch_own_lo[c]);
+      chunks.push_back(m->ch_nsh[c]);
+      chunks.push_back(m->ch_halo_ptr[c]);
+    }
+    chunks.push_back(0);
+    chunks.push_back(0);
+    chunks.push_back(0);
+    chunks.push_back(0);
+    chunks.push_back(0);
+    chunks.push_back(m->ch_halo_ptr.empty() ? 0 : m->ch_halo_ptr.back());
+  }
+  std::vector<int> halo_dev(m->halo_ids.begin(), m->halo_ids.end());
+  if (halo_dev.empty()) halo_dev.push_back(0);
   int rc;
+  if (m->layout == 0 && ((rc = upload(&m->d_chunks, chunks)) || (rc = upload(&m->d_halo, halo_dev)) ||
+                         (rc = upload(&m->d_lconn, m->lconn)))) {
+    fwi_mesh_free(m.release());
+    return rc;
+  }
+  if ((rc = upload(&m->d_bub, m->bub))) {
+    fwi_mesh_free(m.release());
+    return rc;
+  }
   if ((rc = upload(&m->d_conn, conn_dev)) || (rc = upload(&m->d_geo, geo)) ||
       (rc = upload(&m->d_lgeo, lgeo)) || (rc = upload(&m->d_pidx, m->pidx)) ||
       (rc = upload(&m->d_M, m->M))) {
@@ -776,9 +909,9 @@ int fwi_set_velocity(fwi_mesh* m, const double* c) {
     cf[i] = (float)((1.0 - 0.5 * a * dt) / den);
     cf[(size_t)N + i] = (float)(dt * dt / (m->M[i] * den));
     cf[(size_t)2 * N + i] = (float)(dt * dt * m3 / den);
-    const bool in_layer = m->pidx[i] >= 0;
-    mask[i] = (!in_layer && !(m->p.water_speed > 0 && c[i] < m->p.water_speed)) ? 1 : 0;
-    if (in_layer) {
+    const bool damped = tr > 0;
+    mask[i] = (!damped && !(m->p.water_speed > 0 && c[i] < m->p.water_speed)) ? 1 : 0;
+    if (m->pidx[i] >= 0) {
       float* L = &lcf[(size_t)m->pidx[i] * LC];
       for (int k = 0; k < d; ++k) {
         double others = tr - s[k];
@@ -958,6 +1091,22 @@ StepArgs base_args(fwi_batch* b) {
   a.log2S = b->log2S;
   a.Ns = m->Ns;
   a.N = m->N;
+  a.bub = m->d_bub;
+  if (m->layout == 0) {
+    a.nch = m->nch();
+    a.N_own = m->N_own;
+    a.L_max = m->L_max;
+    a.PE = m->P;
+    a.SG = std::min(b->S, 4);
+    a.chunks = m->d_chunks;
+    a.halo = m->d_halo;
+    a.lconn = m->d_lconn;
+    a.h0 = m->N_own;
+    a.hcnt = m->N - m->N_own;
+  } else {
+    a.h0 = 0;
+    a.hcnt = m->Ns;
+  }
   a.nt = b->nt;
   a.dt = (float)m->dt;
   a.conn = m->d_conn;
@@ -999,7 +1148,12 @@ void run_step(fwi_batch* b, const StepArgs& a, cudaStream_t st) {
     }
   }
   if (e) cudaEventRecord(e[0], st);
-  b->m->ks->launch_step(a, st);
+  if (b->m->layout == 0) {
+    int rc = b->m->ks->launch_chunk(a, st);
+    if (rc) b->launch_error = rc;
+  } else {
+    b->m->ks->launch_step(a, st);
+  }
   if (e) cudaEventRecord(e[1], st);
   fwi::launch_node_update(a, b->m->dim, st);
   if (e) cudaEventRecord(e[2], st);
@@ -1058,6 +1212,11 @@ int zero_state(fwi_batch* b, float* u, float* v, float* P, float* Y, cudaStream_
 }
 
 int check_status(fwi_batch* b, cudaStream_t st) {
+  if (b->launch_error) {
+    int e = b->launch_error;
+    b->launch_error = 0;
+    return fail(FWI_ECUDA, std::string("chunk kernel launch: ") + cudaGetErrorString((cudaError_t)e));
+  }
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, b->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -1256,7 +1415,7 @@ int fwi_profile_read(fwi_batch* b, double* ms, int64_t* steps) {
 int fwi_mesh_free(fwi_mesh* m) {
   if (!m) return 0;
   void* ptrs[] = {m->d_conn, m->d_geo, m->d_lgeo, m->d_pidx, m->d_c2, m->d_c, m->d_cf,
-                  m->d_lcf, m->d_M, m->d_mask};
+                  m->d_lcf, m->d_M, m->d_mask, m->d_bub, m->d_chunks, m->d_halo, m->d_lconn};
   for (void* p : ptrs) dfree(p);
   delete m;
   return 0;

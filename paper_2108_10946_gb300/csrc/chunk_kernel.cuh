@@ -1,0 +1,340 @@
+// Chunked time step: one CTA assembles one chunk of consecutive elements (Morton order)
+// for a group of up to 4 shots, entirely in shared memory.
+//
+//   1. load    the chunk's owned DoFs (one contiguous range: its vertex/edge/face DoFs that
+//              no other chunk touches, then its elements' bubble DoFs) with coalesced loads,
+//              and its halo DoFs (shared with other chunks) through the halo list;
+//   2. element one thread per (element, shot): the same stiffness / layer / gradient
+//              arithmetic as the plain kernel (Dhat from the constant bank), gathering from
+//              and scattering into shared memory (shared-memory atomics for the element's
+//              vertex/edge/face nodes, plain stores for its bubble nodes);
+//   3. update  the owned DoFs are final after the chunk's own elements: the increment update
+//              runs here with coalesced reads and writes; halo contributions go to global
+//              accumulators that the node kernel finishes after all chunks.
+//
+// Owned DoFs are read and written by this CTA only, so the in-place update is race free;
+// halo DoFs are only read here and updated by the node kernel afterwards.
+#pragma once
+#include "update.cuh"
+
+namespace fwi {
+
+// floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
+__host__ __device__ inline size_t chunk_smem_floats(int L, int SG, int D, bool grad, bool layer) {
+  size_t f = (size_t)L * (2 * SG + 1);
+  if (grad) f += (size_t)L * (SG + 1);
+  if (layer) f += (size_t)L * D * SG + (D == 3 ? (size_t)L * D * SG + (size_t)L * SG : 0);
+  return f;
+}
+
+template <int D, int NN, int NS>
+__device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
+  constexpr int NI = NN - NS;
+  constexpr int NG = D == 2 ? 3 : 6;
+  typedef LayerCoef<D> LC;
+  const int c = blockIdx.x;
+  const int* ch = a.chunks + 6 * c;
+  const int e0 = ch[0], ne = ch[1], own_lo = ch[2], own_n = ch[3], nsh = ch[4], hp = ch[5];
+  const int hn = a.chunks[6 * (c + 1) + 5] - hp;
+  const int S = a.S;
+  const int SG = a.SG;              // shots of this CTA: [s0, s0 + SG)
+  const int s0 = blockIdx.y * SG;
+  const bool adj = a.mode == 1;
+  const bool grad = adj && a.ring_u != nullptr;
+  const bool layer = e0 >= a.E0;
+  const int Lm = a.L_max;
+  float* uloc = smem;                      // [L][SG]
+  float* yloc = uloc + (size_t)Lm * SG;    // [L][SG]
+  float* c2loc = yloc + (size_t)Lm * SG;   // [L]
+  float* Floc = c2loc + Lm;                // [L][SG] forward field (gradient)
+  float* gloc = Floc + (grad ? (size_t)Lm * SG : 0);          // [L]
+  float* sloc = gloc + (grad ? Lm : 0);                      // [L][D][SG] layer scatter
+  float* sYloc = sloc + (size_t)Lm * D * SG;                 // [L][D][SG] 3D forward
+  float* ywloc = sYloc + (D == 3 ? (size_t)Lm * D * SG : 0);  // [L][SG] 3D adjoint
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  // ---- 1. load -------------------------------------------------------------------------
+  for (int i = tid; i < own_n * SG; i += nth) {
+    const int l = i / SG, s = s0 + (i - l * SG);
+    const size_t g = (size_t)(own_lo + l) * S + s;
+    uloc[i] = a.u[g];
+    yloc[i] = 0.f;
+    if (grad) Floc[i] = __ldg(a.ring_u + g);
+  }
+  for (int i = tid; i < hn * SG; i += nth) {
+    const int h = i / SG, s = s0 + (i - h * SG);
+    const size_t g = (size_t)__ldg(a.halo + hp + h) * S + s;
+    uloc[own_n * SG + i] = a.u[g];
+    yloc[own_n * SG + i] = 0.f;
+    if (grad) Floc[own_n * SG + i] = __ldg(a.ring_u + g);
+  }
+  const int L = own_n + hn;
+  for (int l = tid; l < L; l += nth) {
+    const int dof = l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n);
+    c2loc[l] = __ldg(a.c2 + dof);
+    if (grad) gloc[l] = 0.f;
+  }
+  if (layer) {
+    for (int i = tid; i < L * D * SG; i += nth) {
+      sloc[i] = 0.f;
+      if constexpr (D == 3) sYloc[i] = 0.f;
+    }
+    if constexpr (D == 3)
+      for (int i = tid; i < L * SG; i += nth) ywloc[i] = 0.f;
+  }
+  __syncthreads();
+
+  // ---- 2. elements ---------------------------------------------------------------------
+  const int P = a.PE;
+  const int el = tid % P;
+  const int sl = tid / P;
+  if (el < ne && sl < SG) {
+    const int e = e0 + el;
+    const int s = s0 + sl;
+    int lq[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
+    const int lb = nsh + el * NI;  // local index of the first bubble node
+    auto gdof = [&](int l) { return l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n); };
+    float U[NN], F[NN];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) U[q] = uloc[lq[q] * SG + sl];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) U[NS + j] = uloc[(lb + j) * SG + sl];
+    if (grad) {
+#pragma unroll
+      for (int q = 0; q < NS; ++q) F[q] = Floc[lq[q] * SG + sl];
+#pragma unroll
+      for (int j = 0; j < NI; ++j) F[NS + j] = Floc[(lb + j) * SG + sl];
+    }
+    float G[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) G[g] = __ldg(a.geo + (size_t)g * a.E + e);
+    float Am[D * D];
+    const int El = a.E - a.E0;
+#pragma unroll
+    for (int cc = 0; cc < D * D; ++cc)
+      Am[cc] = layer ? __ldg(a.lgeo + (size_t)cc * El + (e - a.E0)) : 0.f;
+    float Yv[NN];
+#pragma unroll
+    for (int q = 0; q < NN; ++q) Yv[q] = 0.f;
+    if constexpr (D == 3) {
+      if (layer && !adj) {
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+          const int pi = __ldg(a.pidx + gdof(q < NS ? lq[q] : lb + q - NS));
+          Yv[q] = pi >= 0 ? a.Y[(size_t)pi * S + s] : 0.f;
+        }
+      }
+    }
+    float y[NN], yw[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) y[i] = yw[i] = 0.f;
+
+#pragma unroll
+    for (int q = 0; q < NN; ++q) {
+      const int lqq = q < NS ? lq[q] : lb + (q - NS);
+      float g[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        float a0 = 0.f, a1 = 0.f;  // two partial sums: shorter dependent FMA chains
+#pragma unroll
+        for (int j = 0; j < NN; j += 2) a0 = fmaf(c_dhat[(d * NN + q) * NN + j], U[j], a0);
+#pragma unroll
+        for (int j = 1; j < NN; j += 2) a1 = fmaf(c_dhat[(d * NN + q) * NN + j], U[j], a1);
+        g[d] = a0 + a1;
+      }
+      const float wq = c_w[q];
+      const float wc = wq * c2loc[lqq];
+      float f[D];
+      if constexpr (D == 2) {
+        f[0] = wc * (G[0] * g[0] + G[1] * g[1]);
+        f[1] = wc * (G[1] * g[0] + G[2] * g[1]);
+      } else {
+        f[0] = wc * (G[0] * g[0] + G[1] * g[1] + G[2] * g[2]);
+        f[1] = wc * (G[1] * g[0] + G[3] * g[1] + G[4] * g[2]);
+        f[2] = wc * (G[2] * g[0] + G[4] * g[1] + G[5] * g[2]);
+      }
+      if (grad) {
+        float gf[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+          for (int j = 0; j < NN; j += 2) a0 = fmaf(c_dhat[(d * NN + q) * NN + j], F[j], a0);
+#pragma unroll
+          for (int j = 1; j < NN; j += 2) a1 = fmaf(c_dhat[(d * NN + q) * NN + j], F[j], a1);
+          gf[d] = a0 + a1;
+        }
+        float dot;
+        if constexpr (D == 2) {
+          dot = g[0] * (G[0] * gf[0] + G[1] * gf[1]) + g[1] * (G[1] * gf[0] + G[2] * gf[1]);
+        } else {
+          dot = g[0] * (G[0] * gf[0] + G[1] * gf[1] + G[2] * gf[2]) +
+                g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
+                g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
+        }
+        atomicAdd(gloc + lqq, 2.f * __ldg(a.cvel + gdof(lqq)) * wq * dot);
+      }
+      if (layer) {
+        const int pi = __ldg(a.pidx + gdof(lqq));
+        if (pi >= 0) {
+          const float* lc = a.lcf + (size_t)pi * LC::COUNT;
+          float sq[D], pq[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
+            sq[k] = wq * acc;
+            const float raw = a.P[((size_t)pi * D + k) * S + s];
+            pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
+          }
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc += Am[d * D + k] * pq[k];
+            f[d] += wq * acc;
+          }
+          float sY[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) sY[k] = 0.f;
+          if constexpr (D == 3) {
+            if (adj) {
+              float pw[3], fw[3];
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                pw[k] = a.P[((size_t)pi * 3 + k) * S + s] * __ldg(lc + LC::PSI3 + k);
+#pragma unroll
+              for (int d = 0; d < 3; ++d)
+                fw[d] = wq * (Am[d * 3 + 0] * pw[0] + Am[d * 3 + 1] * pw[1] + Am[d * 3 + 2] * pw[2]);
+#pragma unroll
+              for (int i = 0; i < NN; ++i)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) yw[i] = fmaf(c_dhat[(d * NN + q) * NN + i], fw[d], yw[i]);
+            } else {
+              float gy[3];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < NN; ++j) acc = fmaf(c_dhat[(d * NN + q) * NN + j], Yv[j], acc);
+                gy[d] = acc;
+              }
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                sY[k] = wq * (Am[0 * 3 + k] * gy[0] + Am[1 * 3 + k] * gy[1] + Am[2 * 3 + k] * gy[2]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float* sp = sloc + ((size_t)lqq * D + k) * SG + sl;
+            float* syp = sYloc + ((size_t)lqq * D + k) * SG + sl;
+            if (q < NS) {
+              atomicAdd(sp, sq[k]);
+              if constexpr (D == 3) atomicAdd(syp, sY[k]);
+            } else {
+              *sp = sq[k];
+              if constexpr (D == 3) *syp = sY[k];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NN; ++i)
+#pragma unroll
+        for (int d = 0; d < D; ++d) y[i] = fmaf(c_dhat[(d * NN + q) * NN + i], f[d], y[i]);
+    }
+
+    // sources and receivers of this element (flagged elements only)
+    const int slot = __ldg(a.inj + e);
+    if (slot >= 0) {
+      const int rb = __ldg(a.rslot_ptr + slot), re = __ldg(a.rslot_ptr + slot + 1);
+      if (!adj) {
+        if (a.rec != nullptr) {
+          for (int r = rb; r < re; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < NN; ++k) acc = fmaf(__ldg(a.rslot_phi + (size_t)r * NN + k), U[k], acc);
+            a.rec[((size_t)s * (a.nt + 1) + a.n) * a.R + __ldg(a.rslot_rec + r)] = acc;
+          }
+        }
+        if (__ldg(a.src_elem + s) == e) {
+          const float wv = __ldg(a.wavelet + (size_t)s * a.nt + a.n);
+#pragma unroll
+          for (int k = 0; k < NN; ++k) y[k] -= wv * __ldg(a.src_phi + (size_t)s * NN + k);
+        }
+      } else {
+        for (int r = rb; r < re; ++r) {
+          const float res = __ldg(a.resid + ((size_t)s * (a.nt + 1) + a.n) * a.R + __ldg(a.rslot_rec + r));
+#pragma unroll
+          for (int k = 0; k < NN; ++k) y[k] = fmaf(res, __ldg(a.rslot_phi + (size_t)r * NN + k), y[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      atomicAdd(yloc + lq[q] * SG + sl, y[q]);
+      if constexpr (D == 3) {
+        if (layer && adj) atomicAdd(ywloc + lq[q] * SG + sl, yw[q]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+      yloc[(lb + j) * SG + sl] = y[NS + j];
+      if constexpr (D == 3) {
+        if (layer && adj) ywloc[(lb + j) * SG + sl] = yw[NS + j];
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. owned DoFs: final update; halo DoFs: to the global accumulators ----------------
+  for (int i = tid; i < own_n * SG; i += nth) {
+    const int l = i / SG, sl2 = i - l * SG, s = s0 + sl2;
+    float sU[D], sY[D];
+    float ywv = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
+    if (layer) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        sU[k] = sloc[((size_t)l * D + k) * SG + sl2];
+        if constexpr (D == 3) sY[k] = sYloc[((size_t)l * D + k) * SG + sl2];
+      }
+      if constexpr (D == 3) ywv = ywloc[(size_t)l * SG + sl2];
+    }
+    dof_update<D>(a, own_lo + l, s, yloc[i], uloc[i], sU, sY, ywv);
+  }
+  for (int i = tid; i < hn * SG; i += nth) {
+    const int h = i / SG, sl2 = i - h * SG, s = s0 + sl2;
+    const int dof = __ldg(a.halo + hp + h);
+    const int l = own_n + h;
+    atomicAdd(a.r + (size_t)(dof - a.N_own) * S + s, yloc[(size_t)l * SG + sl2]);
+    if (layer) {
+      const int pi = __ldg(a.pidx + dof);
+      if (pi >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          atomicAdd(a.Pacc + ((size_t)pi * D + k) * S + s, sloc[((size_t)l * D + k) * SG + sl2]);
+          if constexpr (D == 3) {
+            if (!adj) atomicAdd(a.PaccY + ((size_t)pi * D + k) * S + s, sYloc[((size_t)l * D + k) * SG + sl2]);
+          }
+        }
+        if constexpr (D == 3) {
+          if (adj) atomicAdd(a.Yacc + (size_t)pi * S + s, ywloc[(size_t)l * SG + sl2]);
+        }
+      }
+    }
+  }
+  if (grad) {
+    for (int l = tid; l < L; l += nth) {
+      // several shot groups (blockIdx.y) add to the same DoF: atomics for all
+      const int dof = l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n);
+      atomicAdd(a.gseg + dof, gloc[l]);
+    }
+  }
+}
+
+}  // namespace fwi

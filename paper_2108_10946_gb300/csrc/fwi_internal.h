@@ -20,6 +20,14 @@ namespace fwi {
 struct StepArgs {
   int E, E0, S, Ns, N;
   int log2S;
+  int h0, hcnt;        // node kernel range: DoFs [h0, h0 + hcnt), r indexed from h0
+  // chunked layout (layout 0)
+  int nch, N_own, L_max, PE, SG;  // chunks, owned DoFs, largest chunk table, elements per
+                                  // chunk, shots per CTA
+  const int* bub;            // [E] first bubble DoF of each element
+  const int* chunks;         // [nch][6]: e0, ne, own_lo, own_n, nsh, halo_ptr
+  const int* halo;           // halo DoF ids, chunk by chunk
+  const unsigned short* lconn;  // [NS][E] chunk-local index of each shared node
   int mode;            // 0 forward, 1 adjoint (with gradient when ring != null)
   int n;               // time index (forward: step n -> n+1; adjoint: step m)
   int nt;
@@ -71,7 +79,8 @@ inline int layer_coef_count(int dim) { return dim == 2 ? 4 * 2 : 6 * 3 + 4; }
 struct KernelSet {
   int dim, k, nn, ns, ni;
   int (*upload_constants)(const float* dhat, const float* w);  // [D][NN][NN], [NN]
-  void (*launch_step)(const StepArgs& a, cudaStream_t st);
+  void (*launch_step)(const StepArgs& a, cudaStream_t st);        // plain layout
+  int (*launch_chunk)(const StepArgs& a, cudaStream_t st);        // chunked layout
   void (*launch_record)(const StepArgs& a, const int* rec_elem, const float* rec_phi,
                         cudaStream_t st);  // d^n for every receiver and shot
 };

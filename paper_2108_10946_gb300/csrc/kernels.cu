@@ -25,7 +25,7 @@ const KernelSet* kernel_set(int dim, int k) {
 }
 
 void launch_node_update(const StepArgs& a, int dim, cudaStream_t st) {
-  const int64_t threads = (int64_t)a.Ns * a.S;
+  const int64_t threads = (int64_t)a.hcnt * a.S;
   if (threads == 0) return;
   const int bs = 256;
   const unsigned blocks = (unsigned)((threads + bs - 1) / bs);

@@ -39,7 +39,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a) {
   const bool adj = a.mode == 1;
   const bool grad = adj && a.ring_u != nullptr;
   const bool layer = e >= a.E0;
-  const int ib = a.Ns + e * NI;
+  const int ib = __ldg(a.bub + e);
 
   int dof[NS];
   float U[NN];
@@ -269,7 +269,7 @@ __global__ void record_kernel(const StepArgs a, const int* rec_elem, const float
     acc = fmaf(__ldg(rec_phi + (size_t)r * NN + q), a.u[(size_t)__ldg(a.conn + (size_t)q * a.E + e) * a.S + s], acc);
 #pragma unroll
   for (int j = 0; j < NI; ++j)
-    acc = fmaf(__ldg(rec_phi + (size_t)r * NN + NS + j), a.u[(size_t)(a.Ns + e * NI + j) * a.S + s], acc);
+    acc = fmaf(__ldg(rec_phi + (size_t)r * NN + NS + j), a.u[(size_t)(__ldg(a.bub + e) + j) * a.S + s], acc);
   a.rec[((size_t)s * (a.nt + 1) + a.n) * a.R + r] = acc;
 }
 

@@ -69,19 +69,23 @@ __device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, fl
 // Shared-DoF finish: y from the atomic accumulator, then the same update.
 template <int D>
 __global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
+  // DoFs [h0, h0 + hcnt): the shared DoFs (plain layout) or the halo DoFs (chunked layout),
+  // whose element contributions arrived by atomics in r[(dof - h0) * S + s]
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = t >> a.log2S;
   const int s = (int)(t & (a.S - 1));
-  if (i >= a.Ns) return;
-  const size_t ix = (size_t)i * a.S + s;
-  const float y = a.r[ix];
-  a.r[ix] = 0.f;
+  if (i >= a.hcnt) return;
+  const int dof = a.h0 + (int)i;
+  const size_t rx = (size_t)i * a.S + s;
+  const size_t ix = (size_t)dof * a.S + s;
+  const float y = a.r[rx];
+  a.r[rx] = 0.f;
   const float uo = a.u[ix];
   float sU[D], sY[D];
   float yw = 0.f;
 #pragma unroll
   for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
-  const int pi = __ldg(a.pidx + i);
+  const int pi = __ldg(a.pidx + dof);
   if (pi >= 0) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
       }
     }
   }
-  dof_update<D>(a, (int)i, s, y, uo, sU, sY, yw);
+  dof_update<D>(a, dof, s, y, uo, sU, sY, yw);
 }
 
 }  // namespace fwi

@@ -27,7 +27,8 @@ class Params(ctypes.Structure):
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
                 ("layer_faces", ctypes.c_int), ("layer_width", ctypes.c_double),
                 ("sigma_max", ctypes.c_double), ("absorbing", ctypes.c_int),
-                ("ckpt_stride", ctypes.c_int), ("water_speed", ctypes.c_double)]
+                ("ckpt_stride", ctypes.c_int), ("water_speed", ctypes.c_double),
+                ("layout", ctypes.c_int)]
 
 
 _lib = None
@@ -136,7 +137,7 @@ class Mesh:
 
     def __init__(self, verts, cells, k, nsteps, dt=0.0, cfl_factor=0.9, box=None, layer_faces=0,
                  layer_width=0.0, sigma_max=0.0, absorbing=False, ckpt_stride=50, water_speed=0.0,
-                 host_only=False):
+                 host_only=False, layout=0):
         lib = load()
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -156,6 +157,7 @@ class Mesh:
         p.absorbing = int(bool(absorbing))
         p.ckpt_stride = int(ckpt_stride)
         p.water_speed = float(water_speed)
+        p.layout = int(layout)
         self.params = p
         self.dim = p.dim
         h = ctypes.c_void_p()

@@ -43,7 +43,7 @@ def _case2d(k, n=12, layer=False):
 
 
 def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=models.smooth2d,
-              f=8.0):
+              f=8.0, layout=0):
     # dt from the oracle's Gershgorin estimate, passed to both sides; T long enough for the
     # direct and reflected arrivals to cross the receivers
     probe = OracleCase(V, C, k, cfun, 1.0, 1, layer=lay, absorbing=absorbing)
@@ -54,7 +54,7 @@ def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=mode
     if lay is not None:
         box = [tuple(b) for b in lay["box"]]
         kw = dict(box=box, layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"])
-    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=absorbing, ckpt_stride=17, **kw)
+    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=absorbing, ckpt_stride=17, layout=layout, **kw)
     xg = mesh.dof_coords()
     perm = match_dofs(orc.mesh.coords, xg, 1.0)  # xg[perm] == oracle coords
     mesh.set_velocity(cfun(xg))
@@ -82,15 +82,17 @@ def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=mode
     return out
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
-def test_forward_records_2d(lib, k):
+def test_forward_records_2d(lib, k, layout):
+    """Both data layouts: chunked shared-memory assembly (0) and plain atomics (1)."""
     V, C, lay = _case2d(k)
     srcs = [[0.5, 0.3], [0.31, 0.62]]
     recs = [[x, 0.85] for x in np.linspace(0.05, 0.95, 9)]
-    o = _run_both(lib, V, C, k, lay, 0.7, srcs, recs, absorbing=False)
+    o = _run_both(lib, V, C, k, lay, 0.7, srcs, recs, absorbing=False, layout=layout)
     for s in range(2):
         err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
-        print(f"k={k} shot {s}: records rel-L2 = {err:.3e}")
+        print(f"k={k} layout={layout} shot {s}: records rel-L2 = {err:.3e}")
         assert err < REC_TOL
 
 
@@ -121,8 +123,9 @@ def test_gershgorin_dt_matches_oracle(lib):
     assert abs(mesh.dt - 0.8 * orc.ops.cfl_dt()) < 1e-12 * mesh.dt
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("k", [2, 3])
-def test_forward_and_gradient_3d_layer(lib, k):
+def test_forward_and_gradient_3d_layer(lib, k, layout):
     """KMV2tet / KMV3tet with the 3D damping layer (u, p in R^3, omega) and the absorbing
     boundary: records and gradient against the oracle."""
     g = np.linspace(0.0, 1.0, 6)
@@ -133,11 +136,11 @@ def test_forward_and_gradient_3d_layer(lib, k):
     srcs = [[0.5, 0.5, 0.1], [0.4, 0.55, 0.15]]
     recs = [[x, y, 0.5] for x in (0.3, 0.5, 0.7) for y in (0.35, 0.65)]
     o = _run_both(lib, V, C, k, lay, 0.5, srcs, recs, absorbing=True, grad=True,
-                  cfun=models.smooth3d, f=6.0)
+                  cfun=models.smooth3d, f=6.0, layout=layout)
     for s in range(2):
         err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
-        print(f"3D k={k} shot {s}: records rel-L2 = {err:.3e}")
+        print(f"3D k={k} layout={layout} shot {s}: records rel-L2 = {err:.3e}")
         assert err < REC_TOL
     gerr = rel_l2(o["G_gpu"], o["G_orc"])
-    print(f"3D k={k}: gradient rel-L2 = {gerr:.3e}")
+    print(f"3D k={k} layout={layout}: gradient rel-L2 = {gerr:.3e}")
     assert gerr < GRAD_TOL
