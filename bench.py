@@ -60,6 +60,13 @@ def make_workload(k=5, C=None, seed=0, nshots=40, nrec=500, T=4.0, f=5.0, small=
                 f=f, box=box)
 
 
+def shots_for_rank(nshots, S, rank, world, step=0):
+    """Shot indices a rank runs at a given step: the shots are dealt round-robin in blocks of
+    S, so that N ranks together cover S*N consecutive shots per step (weak scaling)."""
+    base = (step * world + rank) * S
+    return [(base + i) % nshots for i in range(S)]
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -198,7 +205,7 @@ def run_ours(args):
     mesh.set_velocity(c)
     N, E = mesh.N, wl["cells"].shape[0]
     S = args.shots
-    shots = wl["srcs"][(rank * S + np.arange(S)) % len(wl["srcs"])]
+    shots = wl["srcs"][shots_for_rank(len(wl["srcs"]), S, rank, world)]
     batch = pkg.Batch(mesh, shots, wl["recs"])
     R = len(wl["recs"])
     wav = np.stack([signals.ricker_samples(wl["f"], dt, nt)] * S)

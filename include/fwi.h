@@ -133,6 +133,16 @@ int fwi_get_dt(const fwi_mesh* m, double* dt);
 int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const double* rec,
                      fwi_batch** out);
 
+/* Moves the batch's S sources (src[S][dim] host doubles, located as in fwi_batch_create)
+ * without reallocating; the next call must be fwi_forward_shot. Lets a shot server reuse a
+ * resident batch for new requests on the same mesh and receiver spread. */
+int fwi_batch_set_sources(fwi_batch* b, const double* src);
+
+/* Device bytes fwi_batch_create would allocate for nshots shots and nrec receivers on this
+ * mesh (state, layer auxiliaries, checkpoints, recompute ring, accumulators, signals): the
+ * admission test of a memory-budgeted shot server. */
+int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes);
+
 /* Forward solve, Eq. (forward3) with the readings documented in the design doc, for every shot
  * of the batch. wavelet[S][Nt] floats (w(t_n), n = 0..Nt-1); rec_out[S][Nt+1][R] floats
  * (d^n = H U^n). Stores the checkpoints the adjoint needs. */
@@ -162,6 +172,12 @@ int fwi_profile(fwi_batch* b, int enable);
  * kernel} total milliseconds and steps[2] = {forward+recompute steps, adjoint steps} timed
  * since the last read (then reset). Recompute steps count as forward steps. */
 int fwi_profile_read(fwi_batch* b, double* ms, int64_t* steps);
+
+/* The discrete derivative dJ/dc_i = sum_n 2 c_i sum_e w_i |J_e| grad u_dag . grad u (the
+ * right-hand side of Eq. gradient3 before the mass solve; delta c^T dJ/dc is the directional
+ * derivative of Eq. control_deriv), masked like fwi_gradient. dJdc_out[N] doubles (host or
+ * device), misfit_out may be NULL. Clears the accumulators. */
+int fwi_gradient_raw(fwi_batch* b, double* dJdc_out, double* misfit_out, void* stream);
 
 int fwi_batch_free(fwi_batch* b);
 int fwi_mesh_free(fwi_mesh* m);

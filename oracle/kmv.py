@@ -305,14 +305,15 @@ def newton_orbit_rule(kinds, params0, D, iters=60):
 #   KMV5tri: vertices, two edge pairs, three interior 3-orbits, one interior 6-orbit. No
 #     positive degree-10 rule of this structure was found by multistart search; the
 #     degree-9 (= 2k - 1) equations leave a two-parameter family, fixed here by placing the
-#     edge pairs at t = 0.19 and t = 0.32 (two-digit values near the member of the family
-#     closest to degree-10 exactness); the interior positions and all weights then follow
-#     from the twelve degree-9 equations.
+#     edge pairs at t = 0.19 and t = 0.40: two-digit values of the member with the largest
+#     stable time step (smallest spectral radius of M^-1 K on an equilateral element, the
+#     quantity of Eq. spectral); the interior positions and all weights then follow from
+#     the twelve degree-9 equations.
 _KMV4_KINDS = ["v", "m", "e", "3", "3"]
 _KMV4_START = [0.21, 0.42, 0.13]
 _KMV4_DEGREE = 7
-_KMV5_KINDS = ["v", ("e", 0.19), ("e", 0.32), "3", "3", "3", "6"]
-_KMV5_START = [0.07, 0.48, 0.39, 0.63, 0.27]
+_KMV5_KINDS = ["v", ("e", 0.19), ("e", 0.40), "3", "3", "3", "6"]
+_KMV5_START = [0.08, 0.47, 0.38, 0.61, 0.28]
 _KMV5_DEGREE = 9
 
 

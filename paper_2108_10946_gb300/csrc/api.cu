@@ -113,6 +113,7 @@ struct fwi_mesh {
   int layout = 0;     // 0 chunked (shared-memory assembly), 1 plain (global atomics)
   int P = 32;         // elements per chunk
   int N_own = 0;      // DoFs owned by one chunk: [0, N_own); halo DoFs [N_own, N)
+  int nch0 = 0;       // chunks [0, nch0) have no damping-layer element
   int L_max = 0;      // largest local DoF table of a chunk (owned + halo)
   std::vector<int32_t> bub;                       // [E] first bubble DoF of every element
   std::vector<int32_t> ch_e0, ch_own_lo, ch_nsh;  // chunk element ranges, owned ranges
@@ -341,6 +342,43 @@ int locate(const fwi_mesh* m, const double* pts, int npts, std::vector<int>& use
     for (int c = 0; c < d; ++c) xhat[(size_t)p * d + c] = xh[c];
   }
   return 0;
+}
+
+// Injection slots: every element holding a source of the batch or a receiver gets a slot;
+// a slot lists its receivers (id and basis values). sptr is padded to S + R + 1 entries so
+// that sources can be moved later without reallocating.
+void build_injection(const fwi_mesh* m, const fwi_batch* b, std::vector<int>& inj,
+                     std::vector<int>& sptr, std::vector<int>& srec, std::vector<float>& sphi) {
+  const int n = m->nn, S = b->S, nrec = b->R;
+  inj.assign(m->E, -1);
+  std::vector<int> slot_elems;
+  auto slot_of = [&](int e) {
+    if (inj[e] < 0) {
+      inj[e] = (int)slot_elems.size();
+      slot_elems.push_back(e);
+    }
+    return inj[e];
+  };
+  for (int s = 0; s < S; ++s) slot_of(b->src_elem[s]);
+  for (int r = 0; r < nrec; ++r) slot_of(b->rec_elem[r]);
+  const int ns = (int)slot_elems.size();
+  sptr.assign(S + nrec + 1, 0);
+  srec.clear();
+  sphi.clear();
+  std::vector<std::vector<int>> lists(ns);
+  for (int r = 0; r < nrec; ++r) lists[inj[b->rec_elem[r]]].push_back(r);
+  for (int t = 0; t < ns; ++t) {
+    sptr[t + 1] = sptr[t] + (int)lists[t].size();
+    for (int r : lists[t]) {
+      srec.push_back(r);
+      for (int k = 0; k < n; ++k) sphi.push_back(b->rec_phi[(size_t)r * n + k]);
+    }
+  }
+  for (int t = ns + 1; t < (int)sptr.size(); ++t) sptr[t] = sptr[ns];
+  if (srec.empty()) {
+    srec.push_back(0);
+    sphi.assign(n, 0.f);
+  }
 }
 
 // Gershgorin bound of rho(M^-1 K) on the assembled stiffness (Eq. spectral).
@@ -586,6 +624,7 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
     const int P = m->P;
     m->ch_e0.clear();
     for (int e = 0; e < m->E0; e += P) m->ch_e0.push_back(e);
+    m->nch0 = (int)m->ch_e0.size();
     for (int e = m->E0; e < E; e += P) m->ch_e0.push_back(e);
     m->ch_e0.push_back(E);
     const int nch = (int)m->ch_e0.size() - 1;
@@ -1014,34 +1053,9 @@ int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const
       for (int k = 0; k < n; ++k) b->rec_phi[(size_t)r * n + k] = (float)phi[k];
     }
   }
-  // injection slots: every element holding a source or a receiver
-  std::vector<int> inj(m->E, -1);
-  std::vector<int> slot_elems;
-  auto slot_of = [&](int e) {
-    if (inj[e] < 0) {
-      inj[e] = (int)slot_elems.size();
-      slot_elems.push_back(e);
-    }
-    return inj[e];
-  };
-  for (int s = 0; s < S; ++s) slot_of(b->src_elem[s]);
-  for (int r = 0; r < nrec; ++r) slot_of(b->rec_elem[r]);
-  const int ns = (int)slot_elems.size();
-  std::vector<int> sptr(ns + 1, 0), srec;
+  std::vector<int> inj, sptr, srec;
   std::vector<float> sphi;
-  std::vector<std::vector<int>> lists(ns);
-  for (int r = 0; r < nrec; ++r) lists[inj[b->rec_elem[r]]].push_back(r);
-  for (int t = 0; t < ns; ++t) {
-    sptr[t + 1] = sptr[t] + (int)lists[t].size();
-    for (int r : lists[t]) {
-      srec.push_back(r);
-      for (int k = 0; k < n; ++k) sphi.push_back(b->rec_phi[(size_t)r * n + k]);
-    }
-  }
-  if (srec.empty()) {
-    srec.push_back(0);
-    sphi.assign(n, 0.f);
-  }
+  build_injection(m, b.get(), inj, sptr, srec, sphi);
   std::vector<int> src_elem_dev(b->src_elem.begin(), b->src_elem.end());
   std::vector<int> rec_elem_dev(b->rec_elem.begin(), b->rec_elem.end());
   if (rec_elem_dev.empty()) rec_elem_dev.push_back(0);
@@ -1094,6 +1108,8 @@ StepArgs base_args(fwi_batch* b) {
   a.bub = m->d_bub;
   if (m->layout == 0) {
     a.nch = m->nch();
+    a.nch0 = m->nch0;
+    a.ch0 = 0;
     a.N_own = m->N_own;
     a.L_max = m->L_max;
     a.PE = m->P;
@@ -1231,8 +1247,9 @@ int check_status(fwi_batch* b, cudaStream_t st) {
 
 // Forward steps n0 .. n1-1 on the batch's forward state; optional records and checkpoints.
 void forward_steps(fwi_batch* b, int n0, int n1, const float* wav, float* recs, bool ckpts,
-                   cudaStream_t st) {
+                   cudaStream_t st, float* r_scratch = nullptr) {
   StepArgs a = base_args(b);
+  if (r_scratch) a.r = r_scratch;
   a.mode = 0;
   a.u = b->u;
   a.v = b->v;
@@ -1383,6 +1400,79 @@ int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* strea
   fwi::launch_finish_gradient(b->gsum, b->gcomp, nullptr, b->m->d_M, b->m->d_mask, out, N, st);
   g_launches += 1;
   if (host) CUDA_TRY(cudaMemcpyAsync(grad_out, out, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double J = 0;
+  CUDA_TRY(cudaMemcpyAsync(&J, b->misfit, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (misfit_out) *misfit_out = J;
+  CUDA_TRY(cudaMemsetAsync(b->gsum, 0, (size_t)N * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, (size_t)N * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->misfit, 0, sizeof(double), st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int fwi_batch_set_sources(fwi_batch* b, const double* src) {
+  if (!b || !src) return fail(FWI_EINVAL, "fwi_batch_set_sources: null argument");
+  fwi_mesh* m = b->m;
+  if (int rc = check_device(m)) return rc;
+  const int d = m->dim, n = m->nn, S = b->S;
+  std::vector<int> ue;
+  std::vector<double> xh;
+  if (int rc = locate(m, src, S, ue, xh)) return rc;
+  std::vector<int> new_of_user(m->E);
+  for (int e = 0; e < m->E; ++e) new_of_user[m->order[e]] = e;
+  std::vector<double> phi(n);
+  for (int s = 0; s < S; ++s) {
+    b->src_elem[s] = new_of_user[ue[s]];
+    m->el.basis(&xh[(size_t)s * d], phi.data());
+    for (int k = 0; k < n; ++k) b->src_phi[(size_t)s * n + k] = (float)phi[k];
+  }
+  std::vector<int> inj, sptr, srec;
+  std::vector<float> sphi;
+  build_injection(m, b, inj, sptr, srec, sphi);
+  std::vector<int> se(b->src_elem.begin(), b->src_elem.end());
+  CUDA_TRY(cudaMemcpy(b->d_inj, inj.data(), inj.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_rslot_ptr, sptr.data(), sptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_rslot_rec, srec.data(), srec.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_rslot_phi, sphi.data(), sphi.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_src_elem, se.data(), se.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_src_phi, b->src_phi.data(), b->src_phi.size() * sizeof(float),
+                      cudaMemcpyHostToDevice));
+  b->forward_done = false;
+  return 0;
+}
+
+int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes) {
+  if (!m || !bytes || nshots <= 0) return fail(FWI_EINVAL, "fwi_batch_bytes: bad argument");
+  const int64_t S = nshots, N = m->N, Nl = m->Nl, d = m->dim, nt = m->p.nsteps;
+  const int64_t K = m->p.ckpt_stride, C = (nt + K - 1) / K;
+  const int64_t state = S * (2 * N + Nl * (d + (d == 3 ? 1 : 0)));
+  int64_t f = 0;
+  f += 3 * N * S;                       // u, v, r
+  f += 3 * Nl * d * S + 2 * Nl * S;     // P, Pacc, PaccY, Y, Yacc
+  f += 2 * N * S + Nl * d * S + Nl * S; // adjoint state
+  f += state * C;                       // checkpoints
+  f += N * S * K;                       // recompute ring
+  f += N;                               // FP32 gradient segment
+  f += 2 * S * (nt + 1) * nrec + S * nt;  // records, residual, wavelet copies
+  *bytes = f * 4 + 2 * N * 8 + (int64_t)m->E * 4;
+  return 0;
+}
+
+int fwi_gradient_raw(fwi_batch* b, double* dJdc_out, double* misfit_out, void* stream) {
+  if (!b || !dJdc_out) return fail(FWI_EINVAL, "fwi_gradient_raw: null argument");
+  if (int rc = check_device(b->m)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = b->m->N;
+  double* out = dJdc_out;
+  const bool host = !is_device_ptr(dJdc_out);
+  if (host) {
+    if (!b->stage_grad && dalloc(&b->stage_grad, (size_t)N)) return FWI_ENOMEM;
+    out = b->stage_grad;
+  }
+  fwi::launch_finish_gradient(b->gsum, b->gcomp, nullptr, nullptr, b->m->d_mask, out, N, st);
+  g_launches += 1;
+  if (host) CUDA_TRY(cudaMemcpyAsync(dJdc_out, out, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
   double J = 0;
   CUDA_TRY(cudaMemcpyAsync(&J, b->misfit, sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));

@@ -19,54 +19,62 @@
 
 namespace fwi {
 
+// Row stride of the shot-major shared-memory tables: odd, so that the S rows of one DoF
+// fall in different banks.
+__host__ __device__ inline int chunk_stride(int L) { return L | 1; }
+
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
 __host__ __device__ inline size_t chunk_smem_floats(int L, int SG, int D, bool grad, bool layer) {
-  size_t f = (size_t)L * (2 * SG + 1);
-  if (grad) f += (size_t)L * (SG + 1);
-  if (layer) f += (size_t)L * D * SG + (D == 3 ? (size_t)L * D * SG + (size_t)L * SG : 0);
+  const size_t Ls = (size_t)chunk_stride(L);
+  size_t f = Ls * (2 * SG + 1);
+  if (grad) f += Ls * (SG + 1);
+  if (layer) f += Ls * D * SG + (D == 3 ? Ls * D * SG + Ls * SG : 0);
   return f;
 }
 
-template <int D, int NN, int NS>
+// MODE: 0 forward, 1 adjoint, 2 adjoint with the gradient integrand; LAYER: the chunk's
+// elements touch the damping layer. Separate instances keep each kernel's code small.
+template <int D, int NN, int NS, int MODE, bool LAYER>
 __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   constexpr int NI = NN - NS;
   constexpr int NG = D == 2 ? 3 : 6;
   typedef LayerCoef<D> LC;
-  const int c = blockIdx.x;
+  const int c = blockIdx.x + a.ch0;
   const int* ch = a.chunks + 6 * c;
   const int e0 = ch[0], ne = ch[1], own_lo = ch[2], own_n = ch[3], nsh = ch[4], hp = ch[5];
   const int hn = a.chunks[6 * (c + 1) + 5] - hp;
   const int S = a.S;
   const int SG = a.SG;              // shots of this CTA: [s0, s0 + SG)
   const int s0 = blockIdx.y * SG;
-  const bool adj = a.mode == 1;
-  const bool grad = adj && a.ring_u != nullptr;
-  const bool layer = e0 >= a.E0;
-  const int Lm = a.L_max;
-  float* uloc = smem;                      // [L][SG]
-  float* yloc = uloc + (size_t)Lm * SG;    // [L][SG]
-  float* c2loc = yloc + (size_t)Lm * SG;   // [L]
-  float* Floc = c2loc + Lm;                // [L][SG] forward field (gradient)
-  float* gloc = Floc + (grad ? (size_t)Lm * SG : 0);          // [L]
-  float* sloc = gloc + (grad ? Lm : 0);                      // [L][D][SG] layer scatter
-  float* sYloc = sloc + (size_t)Lm * D * SG;                 // [L][D][SG] 3D forward
-  float* ywloc = sYloc + (D == 3 ? (size_t)Lm * D * SG : 0);  // [L][SG] 3D adjoint
+  constexpr bool adj = MODE != 0;
+  constexpr bool grad = MODE == 2;
+  constexpr bool layer = LAYER;
+  // shot-major tables: entry (l, shot lane s) at s * Lm + l
+  const int Lm = chunk_stride(a.L_max);
+  float* uloc = smem;                      // [SG][Lm]
+  float* yloc = uloc + (size_t)Lm * SG;    // [SG][Lm]
+  float* c2loc = yloc + (size_t)Lm * SG;   // [Lm]
+  float* Floc = c2loc + Lm;                // [SG][Lm] forward field (gradient)
+  float* gloc = Floc + (grad ? (size_t)Lm * SG : 0);          // [Lm]
+  float* sloc = gloc + (grad ? Lm : 0);                      // [D*SG][Lm] layer scatter
+  float* sYloc = sloc + (size_t)Lm * D * SG;                 // [D*SG][Lm] 3D forward
+  float* ywloc = sYloc + (D == 3 ? (size_t)Lm * D * SG : 0);  // [SG][Lm] 3D adjoint
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // ---- 1. load -------------------------------------------------------------------------
   for (int i = tid; i < own_n * SG; i += nth) {
-    const int l = i / SG, s = s0 + (i - l * SG);
-    const size_t g = (size_t)(own_lo + l) * S + s;
-    uloc[i] = a.u[g];
-    yloc[i] = 0.f;
-    if (grad) Floc[i] = __ldg(a.ring_u + g);
+    const int l = i / SG, sl = i - l * SG;
+    const size_t g = (size_t)(own_lo + l) * S + s0 + sl;
+    uloc[sl * Lm + l] = a.u[g];
+    yloc[sl * Lm + l] = 0.f;
+    if (grad) Floc[sl * Lm + l] = __ldg(a.ring_u + g);
   }
   for (int i = tid; i < hn * SG; i += nth) {
-    const int h = i / SG, s = s0 + (i - h * SG);
-    const size_t g = (size_t)__ldg(a.halo + hp + h) * S + s;
-    uloc[own_n * SG + i] = a.u[g];
-    yloc[own_n * SG + i] = 0.f;
-    if (grad) Floc[own_n * SG + i] = __ldg(a.ring_u + g);
+    const int h = i / SG, sl = i - h * SG;
+    const size_t g = (size_t)__ldg(a.halo + hp + h) * S + s0 + sl;
+    uloc[sl * Lm + own_n + h] = a.u[g];
+    yloc[sl * Lm + own_n + h] = 0.f;
+    if (grad) Floc[sl * Lm + own_n + h] = __ldg(a.ring_u + g);
   }
   const int L = own_n + hn;
   for (int l = tid; l < L; l += nth) {
@@ -75,12 +83,12 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     if (grad) gloc[l] = 0.f;
   }
   if (layer) {
-    for (int i = tid; i < L * D * SG; i += nth) {
+    for (int i = tid; i < Lm * D * SG; i += nth) {
       sloc[i] = 0.f;
       if constexpr (D == 3) sYloc[i] = 0.f;
     }
     if constexpr (D == 3)
-      for (int i = tid; i < L * SG; i += nth) ywloc[i] = 0.f;
+      for (int i = tid; i < Lm * SG; i += nth) ywloc[i] = 0.f;
   }
   __syncthreads();
 
@@ -98,14 +106,16 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     auto gdof = [&](int l) { return l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n); };
     float U[NN], F[NN];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) U[q] = uloc[lq[q] * SG + sl];
+    const float* ur = uloc + sl * Lm;
+    for (int q = 0; q < NS; ++q) U[q] = ur[lq[q]];
 #pragma unroll
-    for (int j = 0; j < NI; ++j) U[NS + j] = uloc[(lb + j) * SG + sl];
+    for (int j = 0; j < NI; ++j) U[NS + j] = ur[lb + j];
     if (grad) {
+      const float* fr = Floc + sl * Lm;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) F[q] = Floc[lq[q] * SG + sl];
+      for (int q = 0; q < NS; ++q) F[q] = fr[lq[q]];
 #pragma unroll
-      for (int j = 0; j < NI; ++j) F[NS + j] = Floc[(lb + j) * SG + sl];
+      for (int j = 0; j < NI; ++j) F[NS + j] = fr[lb + j];
     }
     float G[NG];
 #pragma unroll
@@ -229,8 +239,8 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
           }
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            float* sp = sloc + ((size_t)lqq * D + k) * SG + sl;
-            float* syp = sYloc + ((size_t)lqq * D + k) * SG + sl;
+            float* sp = sloc + (size_t)(k * SG + sl) * Lm + lqq;
+            float* syp = sYloc + (size_t)(k * SG + sl) * Lm + lqq;
             if (q < NS) {
               atomicAdd(sp, sq[k]);
               if constexpr (D == 3) atomicAdd(syp, sY[k]);
@@ -273,18 +283,20 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
         }
       }
     }
+    float* yr = yloc + sl * Lm;
+    float* ywr = ywloc + sl * Lm;
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
-      atomicAdd(yloc + lq[q] * SG + sl, y[q]);
+      atomicAdd(yr + lq[q], y[q]);
       if constexpr (D == 3) {
-        if (layer && adj) atomicAdd(ywloc + lq[q] * SG + sl, yw[q]);
+        if (layer && adj) atomicAdd(ywr + lq[q], yw[q]);
       }
     }
 #pragma unroll
     for (int j = 0; j < NI; ++j) {
-      yloc[(lb + j) * SG + sl] = y[NS + j];
+      yr[lb + j] = y[NS + j];
       if constexpr (D == 3) {
-        if (layer && adj) ywloc[(lb + j) * SG + sl] = yw[NS + j];
+        if (layer && adj) ywr[lb + j] = yw[NS + j];
       }
     }
   }
@@ -300,30 +312,30 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     if (layer) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        sU[k] = sloc[((size_t)l * D + k) * SG + sl2];
-        if constexpr (D == 3) sY[k] = sYloc[((size_t)l * D + k) * SG + sl2];
+        sU[k] = sloc[(size_t)(k * SG + sl2) * Lm + l];
+        if constexpr (D == 3) sY[k] = sYloc[(size_t)(k * SG + sl2) * Lm + l];
       }
-      if constexpr (D == 3) ywv = ywloc[(size_t)l * SG + sl2];
+      if constexpr (D == 3) ywv = ywloc[(size_t)sl2 * Lm + l];
     }
-    dof_update<D>(a, own_lo + l, s, yloc[i], uloc[i], sU, sY, ywv);
+    dof_update<D>(a, own_lo + l, s, yloc[sl2 * Lm + l], uloc[sl2 * Lm + l], sU, sY, ywv);
   }
   for (int i = tid; i < hn * SG; i += nth) {
     const int h = i / SG, sl2 = i - h * SG, s = s0 + sl2;
     const int dof = __ldg(a.halo + hp + h);
     const int l = own_n + h;
-    atomicAdd(a.r + (size_t)(dof - a.N_own) * S + s, yloc[(size_t)l * SG + sl2]);
+    atomicAdd(a.r + (size_t)(dof - a.N_own) * S + s, yloc[sl2 * Lm + l]);
     if (layer) {
       const int pi = __ldg(a.pidx + dof);
       if (pi >= 0) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          atomicAdd(a.Pacc + ((size_t)pi * D + k) * S + s, sloc[((size_t)l * D + k) * SG + sl2]);
+          atomicAdd(a.Pacc + ((size_t)pi * D + k) * S + s, sloc[(size_t)(k * SG + sl2) * Lm + l]);
           if constexpr (D == 3) {
-            if (!adj) atomicAdd(a.PaccY + ((size_t)pi * D + k) * S + s, sYloc[((size_t)l * D + k) * SG + sl2]);
+            if (!adj) atomicAdd(a.PaccY + ((size_t)pi * D + k) * S + s, sYloc[(size_t)(k * SG + sl2) * Lm + l]);
           }
         }
         if constexpr (D == 3) {
-          if (adj) atomicAdd(a.Yacc + (size_t)pi * S + s, ywloc[(size_t)l * SG + sl2]);
+          if (adj) atomicAdd(a.Yacc + (size_t)pi * S + s, ywloc[(size_t)sl2 * Lm + l]);
         }
       }
     }

@@ -22,7 +22,7 @@ struct StepArgs {
   int log2S;
   int h0, hcnt;        // node kernel range: DoFs [h0, h0 + hcnt), r indexed from h0
   // chunked layout (layout 0)
-  int nch, N_own, L_max, PE, SG;  // chunks, owned DoFs, largest chunk table, elements per
+  int nch, nch0, ch0, N_own, L_max, PE, SG;  // chunks, owned DoFs, largest chunk table, elements per
                                   // chunk, shots per CTA
   const int* bub;            // [E] first bubble DoF of each element
   const int* chunks;         // [nch][6]: e0, ne, own_lo, own_n, nsh, halo_ptr

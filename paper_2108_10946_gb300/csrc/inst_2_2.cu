@@ -16,27 +16,51 @@ namespace fwi {
 namespace {
 __global__ void __launch_bounds__(128) k_step(const StepArgs a) { step_body<D, NN, NS>(a); }
 
+template <int MODE, bool LAYER>
 __global__ void __launch_bounds__(128) k_chunk(const StepArgs a) {
   extern __shared__ float smem[];
-  chunk_body<D, NN, NS>(a, smem);
+  chunk_body<D, NN, NS, MODE, LAYER>(a, smem);
 }
 
-int launch_chunk(const StepArgs& a, cudaStream_t st) {
-  const bool grad = a.mode == 1 && a.ring_u != nullptr;
-  const bool layer = a.E0 < a.E;
-  const size_t bytes = chunk_smem_floats(a.L_max, a.SG, D, grad, layer) * sizeof(float);
+template <int MODE, bool LAYER>
+int launch_chunk_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
+  if (nch <= 0) return 0;
+  const size_t bytes = chunk_smem_floats(a.L_max, a.SG, D, MODE == 2, LAYER) * sizeof(float);
   if (bytes > 227 * 1024) return (int)cudaErrorInvalidValue;
   static size_t configured[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (bytes > 48 * 1024 && dev < 64 && bytes > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_chunk<MODE, LAYER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     configured[dev] = bytes;
   }
-  dim3 grid((unsigned)a.nch, (unsigned)(a.S / a.SG));
-  k_chunk<<<grid, a.PE * a.SG, bytes, st>>>(a);
+  StepArgs b = a;
+  b.ch0 = ch0;
+  dim3 grid((unsigned)nch, (unsigned)(a.S / a.SG));
+  k_chunk<MODE, LAYER><<<grid, a.PE * a.SG, bytes, st>>>(b);
   return 0;
+}
+
+// chunks [0, nch0) hold no damping-layer element, chunks [nch0, nch) do
+int launch_chunk(const StepArgs& a, cudaStream_t st) {
+  const int mode = a.mode == 0 ? 0 : (a.ring_u != nullptr ? 2 : 1);
+  int rc = 0;
+  switch (mode) {
+    case 0:
+      rc = launch_chunk_t<0, false>(a, 0, a.nch0, st);
+      if (!rc) rc = launch_chunk_t<0, true>(a, a.nch0, a.nch - a.nch0, st);
+      break;
+    case 1:
+      rc = launch_chunk_t<1, false>(a, 0, a.nch0, st);
+      if (!rc) rc = launch_chunk_t<1, true>(a, a.nch0, a.nch - a.nch0, st);
+      break;
+    default:
+      rc = launch_chunk_t<2, false>(a, 0, a.nch0, st);
+      if (!rc) rc = launch_chunk_t<2, true>(a, a.nch0, a.nch - a.nch0, st);
+  }
+  return rc;
 }
 
 int upload(const float* dhat, const float* w) {

@@ -60,7 +60,9 @@ __global__ void finish_kernel(const double* __restrict__ gsum, const double* __r
                               double* __restrict__ out, int64_t N) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  out[i] = mask[i] ? (gsum[i] - gcomp[i]) / M[i] : 0.0;
+  // M == nullptr: the raw discrete derivative dJ/dc (no division by the lumped mass)
+  const double g = gsum[i] - gcomp[i];
+  out[i] = mask[i] ? (M ? g / M[i] : g) : 0.0;
 }
 
 void launch_finish_gradient(const double* gsum, const double* gcomp, const float*,

@@ -66,6 +66,9 @@ def load():
         "fwi_adjoint_misfit": (ctypes.c_int, [_P, _P, _P]),
         "fwi_gradient": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_batch_free": (ctypes.c_int, [_P]),
+        "fwi_batch_set_sources": (ctypes.c_int, [_P, _P]),
+        "fwi_batch_bytes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64)]),
+        "fwi_gradient_raw": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_profile": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_profile_read": (ctypes.c_int, [_P, _P, _P]),
         "fwi_mesh_free": (ctypes.c_int, [_P]),
@@ -212,6 +215,12 @@ class Mesh:
     def nsteps(self):
         return self.params.nsteps
 
+    def batch_bytes(self, nshots, nrec):
+        """Device bytes a batch of nshots shots and nrec receivers would allocate."""
+        v = ctypes.c_int64()
+        _check(_lib.fwi_batch_bytes(self._h, int(nshots), int(nrec), ctypes.byref(v)))
+        return v.value
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.fwi_mesh_free(self._h)
@@ -248,6 +257,19 @@ class Batch:
     def adjoint_misfit(self, observed, stream=None):
         """observed [S][Nt+1][R] float32 (host or device); residual formed on the device."""
         _check(_lib.fwi_adjoint_misfit(self._h, _ptr(observed), _stream_ptr(stream)))
+
+    def set_sources(self, src):
+        """Move the batch's S sources (host coordinates) without reallocating."""
+        src = np.ascontiguousarray(np.atleast_2d(src), dtype=np.float64)
+        if src.shape[0] != self.S:
+            raise ValueError("set_sources needs exactly S positions")
+        _check(_lib.fwi_batch_set_sources(self._h, _ptr(src)))
+
+    def gradient_raw(self, out, stream=None):
+        """out [N] float64 = dJ/dc (masked, no mass solve); returns the misfit J."""
+        J = ctypes.c_double()
+        _check(_lib.fwi_gradient_raw(self._h, _ptr(out), ctypes.byref(J), _stream_ptr(stream)))
+        return J.value
 
     def gradient(self, out, stream=None):
         """out [N] float64 (host or device); returns the misfit J."""
