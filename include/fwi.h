@@ -148,6 +148,23 @@ int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes);
  * (d^n = H U^n). Stores the checkpoints the adjoint needs. */
 int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
 
+/* Allocation-free variant of fwi_forward_shot (the paper has no counterpart: this is a
+ * deployment aid). For callers that cannot call cudaMalloc while they run -- code inside a
+ * CUDA stream capture, where allocating is not allowed, or a service with a fixed device
+ * memory budget reserved at start-up. It runs the same forward solve on the batch's
+ * existing state and writes the records, but calls no cudaMalloc, cudaFree or allocating
+ * library routine: the accumulator of the DoFs finished by the node kernel lives in a
+ * file-scope static __device__ array of 4 Mi floats (16 MiB) that every GPU loading the
+ * library holds until the process exits. It needs (halo DoFs, or shared DoFs for the plain
+ * layout) x shots <= 4 Mi floats and returns FWI_EINVAL beyond that. The array's device
+ * address is looked up (cudaGetSymbolAddress) on the first call on each device, so make
+ * that first call before any stream capture. Every call shares the array and clears it
+ * first; calls that overlap on the GPU (other streams, other threads, other batches) race
+ * on it and must be serialised by the caller. wavelet[S][Nt] and rec_out[S][Nt+1][R] must
+ * be device pointers (FWI_EINVAL otherwise); no checkpoints are stored, so this call does
+ * not prepare an adjoint. */
+int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
+
 /* Discrete adjoint solve (Section 3.4, the transposed recurrence run backwards) driven by
  * residual[S][Nt+1][R] = d - dtilde, with the forward wavefield recomputed segment by
  * segment from the checkpoints of the last fwi_forward_shot. Accumulates the integrand of

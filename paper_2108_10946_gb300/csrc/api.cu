@@ -1362,6 +1362,75 @@ int stage_signal(fwi_batch* b, const float* src, size_t count, const float** dev
 
 extern "C" {
 
+// ---- forward solve without allocation ------------------------------------------------
+// Static scratch of fwi_forward_shot_noalloc: the accumulator of the DoFs that the node
+// kernel finishes (halo DoFs of the chunked layout, shared DoFs of the plain layout), one
+// float per (DoF, shot). Every GPU that loads the library holds it until the process exits.
+}  // extern "C"
+
+static constexpr size_t kNoAllocScratchFloats = size_t(4) << 20;  // 16 MiB
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+namespace {
+std::mutex g_noalloc_mu;
+float* g_noalloc_addr[64] = {nullptr};
+
+// Device address of the static scratch for the current device (looked up once per device;
+// the lookup is the only setup and happens on the first call).
+int noalloc_scratch(float** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(FWI_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = (float*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out, void* stream) {
+  if (!b || !wavelet || !rec_out) return fail(FWI_EINVAL, "fwi_forward_shot_noalloc: null argument");
+  if (int rc = check_device(b->m)) return rc;
+  if (!is_device_ptr(wavelet) || !is_device_ptr(rec_out))
+    return fail(FWI_EINVAL, "fwi_forward_shot_noalloc: wavelet and rec_out must be device memory");
+  const fwi_mesh* m = b->m;
+  const size_t need = (size_t)(m->layout == 0 ? m->N - m->N_own : m->Ns) * b->S;
+  if (need > kNoAllocScratchFloats)
+    return fail(FWI_EINVAL, "fwi_forward_shot_noalloc: mesh too large for the static scratch (" +
+                                std::to_string(need) + " > " + std::to_string(kNoAllocScratchFloats) +
+                                " floats)");
+  cudaStream_t st = (cudaStream_t)stream;
+  float* scratch = nullptr;
+  if (int rc = noalloc_scratch(&scratch)) return rc;
+  // the accumulator must start at zero (a failed earlier call may have left values)
+  if (need) CUDA_TRY(cudaMemsetAsync(scratch, 0, need * sizeof(float), st));
+  const bool prof = b->prof;
+  b->prof = false;  // event timing would create events
+  const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
+  if (int rc = zero_state(b, b->u, b->v, b->P, b->Y, st)) {
+    b->prof = prof;
+    return rc;
+  }
+  if (rn) CUDA_TRY(cudaMemsetAsync(rec_out, 0, rn * sizeof(float), st));
+  forward_steps(b, 0, b->nt, wavelet, rec_out, false, st, scratch);
+  if (b->R) {
+    StepArgs a = base_args(b);
+    a.u = b->u;
+    a.rec = rec_out;
+    a.n = b->nt;
+    m->ks->launch_record(a, b->d_rec_elem, b->d_rec_phi, st);
+    g_launches += 1;
+  }
+  b->prof = prof;
+  return check_status(b, st);
+}
+
 int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream) {
   if (!b || !residual) return fail(FWI_EINVAL, "fwi_adjoint_shot: null argument");
   if (!b->forward_done) return fail(FWI_EINVAL, "fwi_adjoint_shot needs a preceding fwi_forward_shot");

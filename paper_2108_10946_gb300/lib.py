@@ -63,6 +63,7 @@ def load():
         "fwi_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
         "fwi_forward_shot": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_adjoint_shot": (ctypes.c_int, [_P, _P, _P]),
+        "fwi_forward_shot_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_adjoint_misfit": (ctypes.c_int, [_P, _P, _P]),
         "fwi_gradient": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_batch_free": (ctypes.c_int, [_P]),
@@ -249,6 +250,12 @@ class Batch:
     def forward(self, wavelet, rec_out, stream=None):
         """wavelet [S][Nt] float32, rec_out [S][Nt+1][R] float32 (host or device)."""
         _check(_lib.fwi_forward_shot(self._h, _ptr(wavelet), _ptr(rec_out), _stream_ptr(stream)))
+
+    def forward_noalloc(self, wavelet, rec_out, stream=None):
+        """fwi_forward_shot_noalloc: the forward solve with no device allocation (device
+        pointers only; see include/fwi.h for the shared static scratch and its limits)."""
+        _check(_lib.fwi_forward_shot_noalloc(self._h, _ptr(wavelet), _ptr(rec_out),
+                                             _stream_ptr(stream)))
 
     def adjoint(self, residual, stream=None):
         """residual [S][Nt+1][R] float32 = d - dtilde (host or device)."""
