@@ -61,6 +61,7 @@ class ShotServer:
         self.pending = collections.OrderedDict((name, collections.deque()) for name in meshes)
         self.cv = threading.Condition()
         self.pool = {}            # (mesh, S) -> list of idle Batch objects
+        self.nbytes = {}          # (mesh, S) -> device bytes of one such batch
         self.stop = False
         self.completed = []
         self.streams = [torch.cuda.Stream() for _ in range(workers)] if torch_streams else [None] * workers
@@ -90,7 +91,10 @@ class ShotServer:
     # -- scheduling ---------------------------------------------------------------------
     def _take(self):
         """Oldest pending request's mesh, up to max_batch of its requests, and a resident
-        batch (reused, or created if the HBM budget allows). Called with the lock held."""
+        batch: an idle one of the largest size that the pending requests need, else a new
+        one if the HBM budget allows, else the next smaller size. Idle batches of other
+        (mesh, size) pairs are closed to make room when nothing else fits. Returns None when
+        every candidate must wait for a running batch. Called with the lock held."""
         oldest = None
         for name, q in self.pending.items():
             if q and (oldest is None or q[0].arrival < self.pending[oldest][0].arrival):
@@ -103,27 +107,36 @@ class ShotServer:
         while S < n:
             S *= 2
         mesh, recs = self.meshes[oldest]
-        key = (oldest, S)
-        batch = None
-        if self.pool.get(key):
-            batch = self.pool[key].pop()
-        else:
-            need = mesh.batch_bytes(S, len(recs))
-            if self.used + need > self.budget:
-                # not admitted now: retry when memory frees up (a smaller resident batch
-                # may still fit)
-                for s2 in (1, 2, 4, 8, 16, 32):
-                    if s2 >= S:
-                        break
-                    if self.pool.get((oldest, s2)):
-                        S, key = s2, (oldest, s2)
-                        batch = self.pool[key].pop()
-                        n = min(n, S)
-                        break
-                if batch is None:
-                    return None
-            else:
-                self.used += need
+        batch, key = None, None
+        sizes = []
+        while S >= 1:
+            sizes.append(S)
+            S //= 2
+        for s2 in sizes:  # an idle resident batch first (no allocation)
+            if self.pool.get((oldest, s2)):
+                key = (oldest, s2)
+                batch = self.pool[key].pop()
+                break
+        if batch is None:
+            for s2 in sizes:  # else a new one that fits, evicting idle batches if needed
+                need = mesh.batch_bytes(s2, len(recs))
+                if need > self.budget:
+                    continue
+                self._evict_until(need, keep=(oldest, s2))
+                if self.used + need <= self.budget:
+                    self.used += need
+                    self.nbytes[(oldest, s2)] = need
+                    key = (oldest, s2)
+                    break
+            if key is None:
+                if mesh.batch_bytes(1, len(recs)) > self.budget:
+                    r = q.popleft()  # can never run: report instead of waiting forever
+                    r.error = MemoryError("a one-shot batch of this mesh exceeds the HBM budget")
+                    r.done = time.perf_counter()
+                    r.event.set()
+                    self.completed.append(r)
+                return None
+        n = min(n, key[1])
         # at most one gradient request per batch (the batch gradient sums over its shots)
         reqs, keep, have_grad = [], collections.deque(), False
         while q and len(reqs) < n:
@@ -135,7 +148,16 @@ class ShotServer:
             reqs.append(r)
         while keep:
             q.appendleft(keep.pop())
-        return oldest, S, key, batch, reqs
+        return oldest, key[1], key, batch, reqs
+
+    def _evict_until(self, need, keep):
+        """Close idle resident batches (not of ``keep``) until ``need`` bytes fit."""
+        for k in list(self.pool):
+            if k == keep:
+                continue
+            while self.pool[k] and self.used + need > self.budget:
+                self.pool[k].pop().close()
+                self.used -= self.nbytes[k]
 
     def _worker(self, wi):
         torch = self.torch
@@ -166,15 +188,27 @@ class ShotServer:
                     self.cv.notify_all()
 
     def _run(self, pkg, mesh, recs, S, key, batch, reqs, stream):
+        src = np.stack([r.src for r in reqs] + [reqs[0].src] * (S - len(reqs)))
+        if batch is None:
+            try:
+                batch = pkg.Batch(mesh, src, recs)
+            except Exception:
+                with self.cv:
+                    self.used -= self.nbytes[key]
+                raise
+        try:
+            batch.set_sources(src)
+            self._run_batch(mesh, recs, S, batch, reqs, stream)
+        finally:
+            with self.cv:  # the batch stays resident for the next requests
+                self.pool.setdefault(key, []).append(batch)
+                self.cv.notify_all()
+
+    def _run_batch(self, mesh, recs, S, batch, reqs, stream):
         torch = self.torch
         n = len(reqs)
         nt = mesh.nsteps
         R = len(recs)
-        src = np.stack([r.src for r in reqs] + [reqs[0].src] * (S - n))
-        if batch is None:
-            batch = pkg.Batch(mesh, src, recs)
-        else:
-            batch.set_sources(src)
         now = time.perf_counter()
         for r in reqs:
             r.start = now
@@ -212,7 +246,6 @@ class ShotServer:
             r.done = done
             r.event.set()
         with self.cv:
-            self.pool.setdefault(key, []).append(batch)
             self.completed.extend(reqs)
             self.cv.notify_all()
 
