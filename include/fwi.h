@@ -11,6 +11,8 @@
  *       FWI_ENOMEM  (-12)  device or host allocation failed
  *       FWI_ERANGE  (-34)  a non-finite value appeared in the wavefield
  *       FWI_ECUDA   (-5)   a CUDA runtime call failed
+ *       FWI_ETIMEDOUT (-110) a bounded wait inside a kernel gave up (the kernel returned
+ *                          early and reported it; the context stays usable)
  *     fwi_last_error() copies a one-line description of the most recent failure of the
  *     calling thread. Nothing aborts the process.
  *   - Geometry/coordinate arrays (verts, cells, source and receiver positions, velocity)
@@ -39,6 +41,7 @@ extern "C" {
 #define FWI_ENOMEM (-12)
 #define FWI_ERANGE (-34)
 #define FWI_ECUDA (-5)
+#define FWI_ETIMEDOUT (-110)
 
 typedef struct fwi_mesh fwi_mesh;
 typedef struct fwi_batch fwi_batch;
@@ -63,6 +66,11 @@ typedef struct fwi_batch fwi_batch;
  *   layout           0: chunked (elements grouped in chunks that assemble in shared memory;
  *                    the default), 1: plain (one thread per element and shot scattering
  *                    with global atomics; the unfused reference form).
+ *   tensor_cores     chunked layout, triangles only: the per-element derivative
+ *                    contractions (Section 3.2) of a chunk run as tf32 tensor-core MMAs
+ *                    with a three-term hi/lo split (near-FP32 products, FP32 accumulation).
+ *                    0 or -1: off (FP32 CUDA-core arithmetic), 1: on (FWI_EINVAL for
+ *                    tetrahedra or the plain layout).
  */
 typedef struct {
   int dim;
@@ -79,6 +87,7 @@ typedef struct {
   int ckpt_stride;
   double water_speed;
   int layout;
+  int tensor_cores;
 } fwi_params;
 
 /* Builds the DoF numbering, locality order and per-element geometry of a simplex mesh

@@ -111,6 +111,7 @@ struct fwi_mesh {
   int64_t nverts = 0;
   int E = 0, E0 = 0, N = 0, Ns = 0, Nl = 0;
   int layout = 0;     // 0 chunked (shared-memory assembly), 1 plain (global atomics)
+  bool use_tc = false;  // chunked 2D: element contractions on the tensor cores
   int P = 32;         // elements per chunk
   int N_own = 0;      // DoFs owned by one chunk: [0, N_own); halo DoFs [N_own, N)
   int nch0 = 0;       // chunks [0, nch0) have no damping-layer element
@@ -507,6 +508,9 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
   m->ks = ks;
   m->layout = params->layout == 1 ? 1 : 0;
   m->P = d == 2 ? 32 : 16;
+  if (params->tensor_cores > 0 && (d != 2 || m->layout != 0))
+    return fail(FWI_EINVAL, "tensor_cores = 1 needs triangles and the chunked layout");
+  m->use_tc = d == 2 && m->layout == 0 && params->tensor_cores > 0;
   if (!host_only) CUDA_TRY(cudaGetDevice(&m->device));
   std::string err;
   if (!kmvtab::build(d, params->k, m->el, err)) return fail(FWI_EINVAL, "KMV tabulation: " + err);
@@ -1114,6 +1118,7 @@ StepArgs base_args(fwi_batch* b) {
     a.L_max = m->L_max;
     a.PE = m->P;
     a.SG = std::min(b->S, 4);
+    a.tc = m->use_tc ? 1 : 0;
     a.chunks = m->d_chunks;
     a.halo = m->d_halo;
     a.lconn = m->d_lconn;
@@ -1240,6 +1245,7 @@ int check_status(fwi_batch* b, cudaStream_t st) {
   if (b->prof) collect_profile(b);
   if (h) {
     cudaMemsetAsync(b->status, 0, sizeof(int), st);
+    if (h & 2) return fail(FWI_ETIMEDOUT, "a bounded wait on the tensor cores gave up (the kernel returned early)");
     return fail(FWI_ERANGE, "non-finite value in the wavefield (time step above the stability limit?)");
   }
   return 0;

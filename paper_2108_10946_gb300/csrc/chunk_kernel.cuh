@@ -105,8 +105,8 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     const int lb = nsh + el * NI;  // local index of the first bubble node
     auto gdof = [&](int l) { return l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n); };
     float U[NN], F[NN];
-#pragma unroll
     const float* ur = uloc + sl * Lm;
+#pragma unroll
     for (int q = 0; q < NS; ++q) U[q] = ur[lq[q]];
 #pragma unroll
     for (int j = 0; j < NI; ++j) U[NS + j] = ur[lb + j];

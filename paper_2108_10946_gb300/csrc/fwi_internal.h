@@ -28,6 +28,7 @@ struct StepArgs {
   const int* chunks;         // [nch][6]: e0, ne, own_lo, own_n, nsh, halo_ptr
   const int* halo;           // halo DoF ids, chunk by chunk
   const unsigned short* lconn;  // [NS][E] chunk-local index of each shared node
+  int tc;              // chunked layout, 2D: element contraction on the tensor cores
   int mode;            // 0 forward, 1 adjoint (with gradient when ring != null)
   int n;               // time index (forward: step n -> n+1; adjoint: step m)
   int nt;
@@ -62,7 +63,7 @@ struct StepArgs {
   // gradient
   const float* ring_u;     // forward U^m [N][S] (null: no gradient this step)
   float* gseg;             // [N] FP32 segment accumulator
-  int* status;             // bit 0: non-finite value seen
+  int* status;             // bit 0: non-finite value seen; bit 1: a bounded wait gave up
 };
 
 // Layer coefficients per layer DoF (floats):

@@ -1,4 +1,7 @@
 // Kernels for KMV3tri: dim 2, 12 nodes, 9 of them shared (vertex/edge/face).
+#include <algorithm>
+#include <vector>
+
 #include "fwi_internal.h"
 
 namespace fwi {
@@ -11,9 +14,13 @@ __constant__ float c_w[NN];
 
 #include "step_kernel.cuh"
 #include "chunk_kernel.cuh"
+#include "chunk_tc.cuh"
 
 namespace fwi {
 namespace {
+// Dhat as the B operands of the tensor-core kernel (hi and lo, canonical layout)
+__device__ __align__(16) float g_bimg[TcShape<D, NN>::BIMG];
+
 __global__ void __launch_bounds__(128) k_step(const StepArgs a) { step_body<D, NN, NS>(a); }
 
 template <int MODE, bool LAYER>
@@ -43,10 +50,62 @@ int launch_chunk_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   return 0;
 }
 
+template <int MODE, bool LAYER>
+__global__ void __launch_bounds__(128) k_chunk_tc(const StepArgs a, int nrun) {
+  extern __shared__ __align__(128) float smem_tc[];
+  chunk_tc_body<D, NN, NS, MODE, LAYER>(a, smem_tc, g_bimg, nrun);
+}
+
+// persistent: at most two CTAs per SM (each holds 256 of the SM's 512 tensor-memory
+// columns; the shared-memory request is raised so that a third never fits)
+template <int MODE, bool LAYER>
+int launch_chunk_tc_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
+  if (nch <= 0) return 0;
+  size_t bytes = chunk_tc_smem_floats<D, NN>(a.L_max, a.SG, MODE == 2, LAYER) * sizeof(float);
+  if (bytes < 80 * 1024) bytes = 80 * 1024;
+  if (bytes > 227 * 1024) return (int)cudaErrorInvalidValue;
+  static size_t configured[64] = {0};
+  static int nsm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  if (bytes > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_tc<MODE, LAYER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    configured[dev] = bytes;
+  }
+  if (nsm[dev] == 0) {
+    cudaError_t e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+  }
+  StepArgs b = a;
+  b.ch0 = ch0;
+  dim3 grid((unsigned)std::min(nch, 2 * nsm[dev]), (unsigned)(a.S / a.SG));
+  k_chunk_tc<MODE, LAYER><<<grid, a.PE * a.SG, bytes, st>>>(b, nch);
+  return 0;
+}
+
 // chunks [0, nch0) hold no damping-layer element, chunks [nch0, nch) do
 int launch_chunk(const StepArgs& a, cudaStream_t st) {
   const int mode = a.mode == 0 ? 0 : (a.ring_u != nullptr ? 2 : 1);
   int rc = 0;
+  if (a.tc) {
+    switch (mode) {
+      case 0:
+        rc = launch_chunk_tc_t<0, false>(a, 0, a.nch0, st);
+        if (!rc) rc = launch_chunk_tc_t<0, true>(a, a.nch0, a.nch - a.nch0, st);
+        break;
+      case 1:
+        rc = launch_chunk_tc_t<1, false>(a, 0, a.nch0, st);
+        if (!rc) rc = launch_chunk_tc_t<1, true>(a, a.nch0, a.nch - a.nch0, st);
+        break;
+      default:
+        rc = launch_chunk_tc_t<2, false>(a, 0, a.nch0, st);
+        if (!rc) rc = launch_chunk_tc_t<2, true>(a, a.nch0, a.nch - a.nch0, st);
+    }
+    return rc;
+  }
   switch (mode) {
     case 0:
       rc = launch_chunk_t<0, false>(a, 0, a.nch0, st);
@@ -66,6 +125,11 @@ int launch_chunk(const StepArgs& a, cudaStream_t st) {
 int upload(const float* dhat, const float* w) {
   cudaError_t e = cudaMemcpyToSymbol(c_dhat, dhat, sizeof(float) * D * NN * NN);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w, w, sizeof(float) * NN);
+  if (e == cudaSuccess) {
+    std::vector<float> img(TcShape<D, NN>::BIMG);
+    tc_build_bimg<D, NN>(dhat, img.data());
+    e = cudaMemcpyToSymbol(g_bimg, img.data(), sizeof(float) * img.size());
+  }
   return (int)e;
 }
 

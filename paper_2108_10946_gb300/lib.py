@@ -28,7 +28,7 @@ class Params(ctypes.Structure):
                 ("layer_faces", ctypes.c_int), ("layer_width", ctypes.c_double),
                 ("sigma_max", ctypes.c_double), ("absorbing", ctypes.c_int),
                 ("ckpt_stride", ctypes.c_int), ("water_speed", ctypes.c_double),
-                ("layout", ctypes.c_int)]
+                ("layout", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 _lib = None
@@ -141,7 +141,7 @@ class Mesh:
 
     def __init__(self, verts, cells, k, nsteps, dt=0.0, cfl_factor=0.9, box=None, layer_faces=0,
                  layer_width=0.0, sigma_max=0.0, absorbing=False, ckpt_stride=50, water_speed=0.0,
-                 host_only=False, layout=0):
+                 host_only=False, layout=0, tensor_cores=0):
         lib = load()
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -162,6 +162,7 @@ class Mesh:
         p.ckpt_stride = int(ckpt_stride)
         p.water_speed = float(water_speed)
         p.layout = int(layout)
+        p.tensor_cores = int(tensor_cores)
         self.params = p
         self.dim = p.dim
         h = ctypes.c_void_p()

@@ -42,8 +42,12 @@ def _case2d(k, n=12, layer=False):
     return V, C, lay
 
 
+# GPU forms of the time step: (layout, tensor_cores)
+SIMT, TC, PLAIN = (0, -1), (0, 1), (1, 0)
+
+
 def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=models.smooth2d,
-              f=8.0, layout=0):
+              f=8.0, layout=0, tensor_cores=0):
     # dt from the oracle's Gershgorin estimate, passed to both sides; T long enough for the
     # direct and reflected arrivals to cross the receivers
     probe = OracleCase(V, C, k, cfun, 1.0, 1, layer=lay, absorbing=absorbing)
@@ -54,7 +58,8 @@ def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=mode
     if lay is not None:
         box = [tuple(b) for b in lay["box"]]
         kw = dict(box=box, layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"])
-    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=absorbing, ckpt_stride=17, layout=layout, **kw)
+    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=absorbing, ckpt_stride=17, layout=layout,
+                    tensor_cores=tensor_cores, **kw)
     xg = mesh.dof_coords()
     perm = match_dofs(orc.mesh.coords, xg, 1.0)  # xg[perm] == oracle coords
     mesh.set_velocity(cfun(xg))
@@ -82,36 +87,83 @@ def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=mode
     return out
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("form", [SIMT, TC, PLAIN], ids=["chunked", "chunked-tc", "plain"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
-def test_forward_records_2d(lib, k, layout):
-    """Both data layouts: chunked shared-memory assembly (0) and plain atomics (1)."""
+def test_forward_records_2d(lib, k, form):
+    """Every form of the step: chunked shared-memory assembly with FP32 CUDA-core or
+    tensor-core contractions, and plain global atomics."""
     V, C, lay = _case2d(k)
     srcs = [[0.5, 0.3], [0.31, 0.62]]
     recs = [[x, 0.85] for x in np.linspace(0.05, 0.95, 9)]
-    o = _run_both(lib, V, C, k, lay, 0.7, srcs, recs, absorbing=False, layout=layout)
+    o = _run_both(lib, V, C, k, lay, 0.7, srcs, recs, absorbing=False, layout=form[0],
+                  tensor_cores=form[1])
     for s in range(2):
         err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
-        print(f"k={k} layout={layout} shot {s}: records rel-L2 = {err:.3e}")
+        print(f"k={k} form={form} shot {s}: records rel-L2 = {err:.3e}")
         assert err < REC_TOL
 
 
+@pytest.mark.parametrize("form", [SIMT, TC], ids=["chunked", "chunked-tc"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
-def test_forward_and_gradient_2d_layer(lib, k):
+def test_forward_and_gradient_2d_layer(lib, k, form):
     V, C, lay = _case2d(k, n=12, layer=True)
     srcs = [[0.5, 0.1], [0.2, 0.15]]
     recs = [[x, 0.9] for x in np.linspace(0.05, 0.95, 11)]
-    o = _run_both(lib, V, C, k, lay, 0.7, srcs, recs, absorbing=True, grad=True)
+    o = _run_both(lib, V, C, k, lay, 0.7, srcs, recs, absorbing=True, grad=True, layout=form[0],
+                  tensor_cores=form[1])
     for s in range(2):
         err = rel_l2(o["rec_gpu"][s], o["rec_orc"][s])
-        print(f"k={k} layer shot {s}: records rel-L2 = {err:.3e}")
+        print(f"k={k} form={form} layer shot {s}: records rel-L2 = {err:.3e}")
         assert err < REC_TOL
     gerr = rel_l2(o["G_gpu"], o["G_orc"])
-    print(f"k={k} layer: gradient rel-L2 = {gerr:.3e}, J {o['J']:.6e} vs {o['J_ref']:.6e}")
+    print(f"k={k} form={form} layer: gradient rel-L2 = {gerr:.3e}, J {o['J']:.6e} vs {o['J_ref']:.6e}")
     assert gerr < GRAD_TOL
     assert abs(o["J"] - o["J_ref"]) < 1e-10 * abs(o["J_ref"])
     # masked entries are exactly zero on both sides
     assert np.all(o["G_gpu"][~o["orc"].mask] == 0)
+
+
+@pytest.mark.parametrize("S", [1, 4, 8])
+@pytest.mark.parametrize("k", [4, 5])
+def test_tensor_core_step_matches_cuda_core_step(lib, k, S):
+    """Shot counts the oracle cases above do not reach (one shot per CTA row group, a full
+    128-row tile, two shot groups per chunk): the tensor-core step against the FP32 CUDA-core
+    step (itself held to the oracle above), records and gradient, with a damping layer, an
+    absorbing boundary and chunks that straddle the layer."""
+    V, C, lay = _case2d(k, n=14, layer=True)
+    dt = 0.8 * OracleCase(V, C, k, models.smooth2d, 1.0, 1, layer=lay, absorbing=True).ops.cfl_dt()
+    nt = int(round(0.6 / dt))
+    rng = np.random.default_rng(S)
+    srcs = np.column_stack([rng.uniform(0.1, 0.9, S), rng.uniform(0.05, 0.3, S)])
+    recs = np.array([[x, 0.9] for x in np.linspace(0.05, 0.95, 13)])
+    wav = np.stack([signals.ricker_samples(rng.uniform(6, 9), dt, nt, t0=0.15) for _ in range(S)])
+    box = [tuple(b) for b in lay["box"]]
+    out = {}
+    for name, tcf in (("cuda", -1), ("tc", 1)):
+        mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=True, ckpt_stride=17, box=box,
+                        layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"],
+                        tensor_cores=tcf)
+        xg = mesh.dof_coords()
+        mesh.set_velocity(models.smooth2d(xg))
+        batch = lib.Batch(mesh, srcs, recs)
+        rec = torch.zeros((S, nt + 1, len(recs)), device="cuda")
+        batch.forward(torch.from_numpy(wav).float().cuda(), rec)
+        res = (0.1 * rec).contiguous()
+        batch.adjoint(res)
+        G = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+        batch.gradient(G)
+        out[name] = (rec.cpu().numpy(), G.cpu().numpy(), xg)
+        batch.close()
+        mesh.close()
+    (rc, Gc, xc), (rt, Gt, xt) = out["cuda"], out["tc"]
+    assert np.array_equal(xc, xt)
+    for s in range(S):
+        err = rel_l2(rt[s], rc[s])
+        print(f"k={k} S={S} shot {s}: tensor-core vs CUDA-core records rel-L2 = {err:.3e}")
+        assert err < REC_TOL
+    gerr = rel_l2(Gt, Gc)
+    print(f"k={k} S={S}: tensor-core vs CUDA-core gradient rel-L2 = {gerr:.3e}")
+    assert gerr < GRAD_TOL
 
 
 def test_gershgorin_dt_matches_oracle(lib):

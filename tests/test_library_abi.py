@@ -53,3 +53,24 @@ def test_library_tabulation_matches_oracle(dim, k):
     assert np.allclose(e.nodes[perm], xh, atol=1e-13)
     assert np.allclose(e.weights[perm], w, atol=1e-14)
     assert np.allclose(e.Dhat[:, perm][:, :, perm], dh, atol=1e-9)
+
+
+@pytest.mark.parametrize("dim,layout", [(2, 1), (3, 0)])
+def test_tensor_cores_refused_where_there_is_no_such_kernel(dim, layout):
+    """tensor_cores = 1 asks for the tensor-core chunk kernel, which exists for triangles in
+    the chunked layout only; the mesh call refuses anything else (host-only preparation, no
+    GPU needed)."""
+    import numpy as np
+    import paper_2108_10946_gb300 as pkg
+    from synth import meshes
+    pkg.build()
+    if dim == 2:
+        V, C = meshes.structured_tri(4, 4)
+    else:
+        g = np.linspace(0.0, 1.0, 3)
+        V, C = meshes.kuhn_tets(g, g, g)
+    with pytest.raises(RuntimeError, match="tensor_cores"):
+        pkg.Mesh(V, C, 2, 10, dt=1e-3, host_only=True, layout=layout, tensor_cores=1)
+    m = pkg.Mesh(V, C, 2, 10, dt=1e-3, host_only=True, layout=layout, tensor_cores=0)
+    assert m.N > 0
+    m.close()
