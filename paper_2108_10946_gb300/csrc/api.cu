@@ -1178,7 +1178,9 @@ void run_step(fwi_batch* b, const StepArgs& a, cudaStream_t st) {
   if (e) cudaEventRecord(e[1], st);
   fwi::launch_node_update(a, b->m->dim, st);
   if (e) cudaEventRecord(e[2], st);
-  g_launches += 2;
+  // chunked layout: one launch per non-empty chunk class (without / with layer elements)
+  const fwi_mesh* m = b->m;
+  g_launches += 1 + (m->layout == 0 ? (m->nch0 > 0) + (m->nch() > m->nch0) : 1);
 }
 
 // Adds the recorded event intervals to the batch's totals (the stream must be complete).

@@ -1,0 +1,198 @@
+// Global <-> shared-memory traffic of one chunk, shared by the CUDA-core and the tensor-core
+// chunk kernels.
+//
+// Phase 1 (chunk_load) issues every global read of the chunk at once as asynchronous copies
+// (cp.async, 4 bytes each) into the chunk table, in two completion groups: group 0 holds what
+// the element phase reads (u, c^2 and the layer index of every local DoF; the forward field
+// and c of every local DoF in gradient steps), group 1 what only the final update reads (v
+// and the update coefficients c1..c3 of the owned DoFs), so that group 1's latency hides
+// behind the element phase. Phase 3 (chunk_store) finishes the owned DoFs from the table
+// and sends the halo DoFs' contributions to the global accumulators.
+//
+// Table layout (floats, shot-major [SG][Lm] with Lm odd so that the SG rows of one DoF fall
+// in different banks): u, y, v [SG][Lm]; c2 [Lm]; cf [3][Lm]; pi [Lm] (int); gradient
+// steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm] (and in 3D sY [D][SG][Lm],
+// yw [SG][Lm]).
+#pragma once
+#include "update.cuh"
+
+namespace fwi {
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Row stride of the shot-major tables: odd, so that the S rows of one DoF fall in
+// different banks.
+__host__ __device__ inline int chunk_stride(int L) { return L | 1; }
+
+__host__ __device__ inline size_t chunk_tab_floats(int L, int SG, int D, bool grad, bool layer) {
+  const size_t Lm = (size_t)chunk_stride(L);
+  size_t f = Lm * (3 * (size_t)SG + 5);
+  if (grad) f += Lm * ((size_t)SG + 2);
+  if (layer) f += Lm * D * SG + (D == 3 ? Lm * D * SG + Lm * SG : 0);
+  return f;
+}
+
+struct ChunkTab {
+  float *u, *y, *v, *c2, *cf, *F, *g, *cv, *s, *sY, *yw;
+  int* pi;
+};
+
+__device__ __forceinline__ ChunkTab chunk_tab(float* base, int Lm, int SG, int D, bool grad,
+                                              bool layer) {
+  ChunkTab t;
+  const size_t R = (size_t)Lm * SG;
+  t.u = base;
+  t.y = t.u + R;
+  t.v = t.y + R;
+  t.c2 = t.v + R;
+  t.cf = t.c2 + Lm;
+  t.pi = reinterpret_cast<int*>(t.cf + 3 * (size_t)Lm);
+  float* p = reinterpret_cast<float*>(t.pi + Lm);
+  t.F = p;
+  t.g = t.F + (grad ? R : 0);
+  t.cv = t.g + (grad ? Lm : 0);
+  p = t.cv + (grad ? Lm : 0);
+  t.s = p;
+  t.sY = t.s + (layer ? (size_t)D * R : 0);
+  t.yw = t.sY + (layer && D == 3 ? (size_t)D * R : 0);
+  return t;
+}
+
+struct ChunkDesc {
+  int e0, ne, own_lo, own_n, nsh, hp, hn, L;
+};
+
+__device__ __forceinline__ ChunkDesc chunk_desc(const StepArgs& a, int c) {
+  const int* ch = a.chunks + 6 * c;
+  ChunkDesc d;
+  d.e0 = ch[0];
+  d.ne = ch[1];
+  d.own_lo = ch[2];
+  d.own_n = ch[3];
+  d.nsh = ch[4];
+  d.hp = ch[5];
+  d.hn = a.chunks[6 * (c + 1) + 5] - d.hp;
+  d.L = d.own_n + d.hn;
+  return d;
+}
+
+// Phase 1: issue the chunk's reads (two cp.async groups, see above) and clear the
+// accumulators. lg = log2(SG); shots [s0, s0 + SG).
+template <int D, bool GRAD, bool LAYER>
+__device__ __forceinline__ void chunk_load(const StepArgs& a, const ChunkDesc& cd, const ChunkTab& t,
+                                           int Lm, int SG, int lg, int s0, int tid, int nth) {
+  const int S = a.S;
+  const size_t N = (size_t)a.N;
+  for (int i = tid; i < cd.own_n * SG; i += nth) {
+    const int l = i >> lg, q = i & (SG - 1);
+    const size_t g = (size_t)(cd.own_lo + l) * S + s0 + q;
+    cp_async4(t.u + q * Lm + l, a.u + g);
+    if (GRAD) cp_async4(t.F + q * Lm + l, a.ring_u + g);
+  }
+  for (int i = tid; i < cd.hn * SG; i += nth) {
+    const int h = i >> lg, q = i & (SG - 1);
+    const size_t g = (size_t)__ldg(a.halo + cd.hp + h) * S + s0 + q;
+    cp_async4(t.u + q * Lm + cd.own_n + h, a.u + g);
+    if (GRAD) cp_async4(t.F + q * Lm + cd.own_n + h, a.ring_u + g);
+  }
+  for (int l = tid; l < cd.L; l += nth) {
+    const int dof = l < cd.own_n ? cd.own_lo + l : __ldg(a.halo + cd.hp + l - cd.own_n);
+    cp_async4(t.c2 + l, a.c2 + dof);
+    cp_async4(t.pi + l, a.pidx + dof);
+    if (GRAD) cp_async4(t.cv + l, a.cvel + dof);
+  }
+  cp_async_commit();
+  for (int i = tid; i < cd.own_n * SG; i += nth) {
+    const int l = i >> lg, q = i & (SG - 1);
+    cp_async4(t.v + q * Lm + l, a.v + (size_t)(cd.own_lo + l) * S + s0 + q);
+  }
+  for (int l = tid; l < cd.own_n; l += nth) {
+    const size_t dof = (size_t)(cd.own_lo + l);
+    cp_async4(t.cf + l, a.cf + dof);
+    cp_async4(t.cf + Lm + l, a.cf + N + dof);
+    cp_async4(t.cf + 2 * (size_t)Lm + l, a.cf + 2 * N + dof);
+  }
+  cp_async_commit();
+  for (int i = tid; i < cd.L * SG; i += nth) {
+    const int l = i >> lg, q = i & (SG - 1);
+    t.y[q * Lm + l] = 0.f;
+  }
+  if (GRAD)
+    for (int l = tid; l < cd.L; l += nth) t.g[l] = 0.f;
+  if (LAYER) {
+    for (int i = tid; i < Lm * D * SG; i += nth) {
+      t.s[i] = 0.f;
+      if constexpr (D == 3) t.sY[i] = 0.f;
+    }
+    if constexpr (D == 3)
+      for (int i = tid; i < Lm * SG; i += nth) t.yw[i] = 0.f;
+  }
+}
+
+// Phase 3: owned DoFs final (the increment update from the table), halo DoFs to the
+// global accumulators (finished by the node kernel after all chunks), gradient segment.
+// Call after cp_async_wait<0>() and a barrier.
+template <int D, bool GRAD, bool LAYER>
+__device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& cd, const ChunkTab& t,
+                                            int Lm, int SG, int lg, int s0, int tid, int nth) {
+  const int S = a.S;
+  const bool adj = a.mode != 0;
+  for (int i = tid; i < cd.own_n * SG; i += nth) {
+    const int l = i >> lg, q = i & (SG - 1), s = s0 + q;
+    float sU[D], sY[D];
+    float ywv = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
+    if (LAYER) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        sU[k] = t.s[(size_t)(k * SG + q) * Lm + l];
+        if constexpr (D == 3) sY[k] = t.sY[(size_t)(k * SG + q) * Lm + l];
+      }
+      if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
+    }
+    dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], t.v[q * Lm + l],
+                      t.cf[l], t.cf[Lm + l], t.cf[2 * (size_t)Lm + l], LAYER ? t.pi[l] : -1, sU, sY,
+                      ywv);
+  }
+  for (int i = tid; i < cd.hn * SG; i += nth) {
+    const int h = i >> lg, q = i & (SG - 1), s = s0 + q;
+    const int l = cd.own_n + h;
+    const int dof = __ldg(a.halo + cd.hp + h);
+    atomicAdd(a.r + (size_t)(dof - a.N_own) * S + s, t.y[q * Lm + l]);
+    if (LAYER) {
+      const int pi = t.pi[l];
+      if (pi >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          atomicAdd(a.Pacc + ((size_t)pi * D + k) * S + s, t.s[(size_t)(k * SG + q) * Lm + l]);
+          if constexpr (D == 3) {
+            if (!adj) atomicAdd(a.PaccY + ((size_t)pi * D + k) * S + s, t.sY[(size_t)(k * SG + q) * Lm + l]);
+          }
+        }
+        if constexpr (D == 3) {
+          if (adj) atomicAdd(a.Yacc + (size_t)pi * S + s, t.yw[(size_t)q * Lm + l]);
+        }
+      }
+    }
+  }
+  if (GRAD) {
+    for (int l = tid; l < cd.L; l += nth) {
+      // several shot groups (blockIdx.y) add to the same DoF: atomics for all
+      const int dof = l < cd.own_n ? cd.own_lo + l : __ldg(a.halo + cd.hp + l - cd.own_n);
+      atomicAdd(a.gseg + dof, t.g[l]);
+    }
+  }
+}
+
+}  // namespace fwi

@@ -1,35 +1,28 @@
 // Chunked time step: one CTA assembles one chunk of consecutive elements (Morton order)
 // for a group of up to 4 shots, entirely in shared memory.
 //
-//   1. load    the chunk's owned DoFs (one contiguous range: its vertex/edge/face DoFs that
-//              no other chunk touches, then its elements' bubble DoFs) with coalesced loads,
-//              and its halo DoFs (shared with other chunks) through the halo list;
+//   1. load    every global read of the chunk issued at once as asynchronous copies into
+//              the chunk table (chunk_io.cuh): its owned DoFs (one contiguous range: its
+//              vertex/edge/face DoFs that no other chunk touches, then its elements' bubble
+//              DoFs) and its halo DoFs (shared with other chunks, through the halo list);
 //   2. element one thread per (element, shot): the same stiffness / layer / gradient
 //              arithmetic as the plain kernel (Dhat from the constant bank), gathering from
 //              and scattering into shared memory (shared-memory atomics for the element's
 //              vertex/edge/face nodes, plain stores for its bubble nodes);
 //   3. update  the owned DoFs are final after the chunk's own elements: the increment update
-//              runs here with coalesced reads and writes; halo contributions go to global
-//              accumulators that the node kernel finishes after all chunks.
+//              runs here with coalesced writes; halo contributions go to global accumulators
+//              that the node kernel finishes after all chunks.
 //
 // Owned DoFs are read and written by this CTA only, so the in-place update is race free;
 // halo DoFs are only read here and updated by the node kernel afterwards.
 #pragma once
-#include "update.cuh"
+#include "chunk_io.cuh"
 
 namespace fwi {
 
-// Row stride of the shot-major shared-memory tables: odd, so that the S rows of one DoF
-// fall in different banks.
-__host__ __device__ inline int chunk_stride(int L) { return L | 1; }
-
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
 __host__ __device__ inline size_t chunk_smem_floats(int L, int SG, int D, bool grad, bool layer) {
-  const size_t Ls = (size_t)chunk_stride(L);
-  size_t f = Ls * (2 * SG + 1);
-  if (grad) f += Ls * (SG + 1);
-  if (layer) f += Ls * D * SG + (D == 3 ? Ls * D * SG + Ls * SG : 0);
-  return f;
+  return chunk_tab_floats(L, SG, D, grad, layer);
 }
 
 // MODE: 0 forward, 1 adjoint, 2 adjoint with the gradient integrand; LAYER: the chunk's
@@ -49,47 +42,26 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   constexpr bool adj = MODE != 0;
   constexpr bool grad = MODE == 2;
   constexpr bool layer = LAYER;
-  // shot-major tables: entry (l, shot lane s) at s * Lm + l
   const int Lm = chunk_stride(a.L_max);
-  float* uloc = smem;                      // [SG][Lm]
-  float* yloc = uloc + (size_t)Lm * SG;    // [SG][Lm]
-  float* c2loc = yloc + (size_t)Lm * SG;   // [Lm]
-  float* Floc = c2loc + Lm;                // [SG][Lm] forward field (gradient)
-  float* gloc = Floc + (grad ? (size_t)Lm * SG : 0);          // [Lm]
-  float* sloc = gloc + (grad ? Lm : 0);                      // [D*SG][Lm] layer scatter
-  float* sYloc = sloc + (size_t)Lm * D * SG;                 // [D*SG][Lm] 3D forward
-  float* ywloc = sYloc + (D == 3 ? (size_t)Lm * D * SG : 0);  // [SG][Lm] 3D adjoint
+  const int lg = __ffs(SG) - 1;
+  const ChunkTab t = chunk_tab(smem, Lm, SG, D, grad, layer);
+  float* uloc = t.u;
+  float* yloc = t.y;
+  float* c2loc = t.c2;
+  float* Floc = t.F;
+  float* gloc = t.g;
+  float* sloc = t.s;
+  float* sYloc = t.sY;
+  float* ywloc = t.yw;
+  const int* piloc = t.pi;
   const int tid = threadIdx.x, nth = blockDim.x;
+  ChunkDesc cd;
+  cd.e0 = e0, cd.ne = ne, cd.own_lo = own_lo, cd.own_n = own_n, cd.nsh = nsh, cd.hp = hp;
+  cd.hn = hn, cd.L = own_n + hn;
 
   // ---- 1. load -------------------------------------------------------------------------
-  for (int i = tid; i < own_n * SG; i += nth) {
-    const int l = i / SG, sl = i - l * SG;
-    const size_t g = (size_t)(own_lo + l) * S + s0 + sl;
-    uloc[sl * Lm + l] = a.u[g];
-    yloc[sl * Lm + l] = 0.f;
-    if (grad) Floc[sl * Lm + l] = __ldg(a.ring_u + g);
-  }
-  for (int i = tid; i < hn * SG; i += nth) {
-    const int h = i / SG, sl = i - h * SG;
-    const size_t g = (size_t)__ldg(a.halo + hp + h) * S + s0 + sl;
-    uloc[sl * Lm + own_n + h] = a.u[g];
-    yloc[sl * Lm + own_n + h] = 0.f;
-    if (grad) Floc[sl * Lm + own_n + h] = __ldg(a.ring_u + g);
-  }
-  const int L = own_n + hn;
-  for (int l = tid; l < L; l += nth) {
-    const int dof = l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n);
-    c2loc[l] = __ldg(a.c2 + dof);
-    if (grad) gloc[l] = 0.f;
-  }
-  if (layer) {
-    for (int i = tid; i < Lm * D * SG; i += nth) {
-      sloc[i] = 0.f;
-      if constexpr (D == 3) sYloc[i] = 0.f;
-    }
-    if constexpr (D == 3)
-      for (int i = tid; i < Lm * SG; i += nth) ywloc[i] = 0.f;
-  }
+  chunk_load<D, grad, layer>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+  cp_async_wait<1>();
   __syncthreads();
 
   // ---- 2. elements ---------------------------------------------------------------------
@@ -103,7 +75,6 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
 #pragma unroll
     for (int q = 0; q < NS; ++q) lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
     const int lb = nsh + el * NI;  // local index of the first bubble node
-    auto gdof = [&](int l) { return l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n); };
     float U[NN], F[NN];
     const float* ur = uloc + sl * Lm;
 #pragma unroll
@@ -132,7 +103,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
       if (layer && !adj) {
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
-          const int pi = __ldg(a.pidx + gdof(q < NS ? lq[q] : lb + q - NS));
+          const int pi = piloc[q < NS ? lq[q] : lb + q - NS];
           Yv[q] = pi >= 0 ? a.Y[(size_t)pi * S + s] : 0.f;
         }
       }
@@ -184,10 +155,10 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
                 g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
                 g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
         }
-        atomicAdd(gloc + lqq, 2.f * __ldg(a.cvel + gdof(lqq)) * wq * dot);
+        atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
       }
       if (layer) {
-        const int pi = __ldg(a.pidx + gdof(lqq));
+        const int pi = piloc[lqq];
         if (pi >= 0) {
           const float* lc = a.lcf + (size_t)pi * LC::COUNT;
           float sq[D], pq[D];
@@ -303,50 +274,9 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   __syncthreads();
 
   // ---- 3. owned DoFs: final update; halo DoFs: to the global accumulators ----------------
-  for (int i = tid; i < own_n * SG; i += nth) {
-    const int l = i / SG, sl2 = i - l * SG, s = s0 + sl2;
-    float sU[D], sY[D];
-    float ywv = 0.f;
-#pragma unroll
-    for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
-    if (layer) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        sU[k] = sloc[(size_t)(k * SG + sl2) * Lm + l];
-        if constexpr (D == 3) sY[k] = sYloc[(size_t)(k * SG + sl2) * Lm + l];
-      }
-      if constexpr (D == 3) ywv = ywloc[(size_t)sl2 * Lm + l];
-    }
-    dof_update<D>(a, own_lo + l, s, yloc[sl2 * Lm + l], uloc[sl2 * Lm + l], sU, sY, ywv);
-  }
-  for (int i = tid; i < hn * SG; i += nth) {
-    const int h = i / SG, sl2 = i - h * SG, s = s0 + sl2;
-    const int dof = __ldg(a.halo + hp + h);
-    const int l = own_n + h;
-    atomicAdd(a.r + (size_t)(dof - a.N_own) * S + s, yloc[sl2 * Lm + l]);
-    if (layer) {
-      const int pi = __ldg(a.pidx + dof);
-      if (pi >= 0) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          atomicAdd(a.Pacc + ((size_t)pi * D + k) * S + s, sloc[(size_t)(k * SG + sl2) * Lm + l]);
-          if constexpr (D == 3) {
-            if (!adj) atomicAdd(a.PaccY + ((size_t)pi * D + k) * S + s, sYloc[(size_t)(k * SG + sl2) * Lm + l]);
-          }
-        }
-        if constexpr (D == 3) {
-          if (adj) atomicAdd(a.Yacc + (size_t)pi * S + s, ywloc[(size_t)sl2 * Lm + l]);
-        }
-      }
-    }
-  }
-  if (grad) {
-    for (int l = tid; l < L; l += nth) {
-      // several shot groups (blockIdx.y) add to the same DoF: atomics for all
-      const int dof = l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n);
-      atomicAdd(a.gseg + dof, gloc[l]);
-    }
-  }
+  cp_async_wait<0>();
+  __syncthreads();
+  chunk_store<D, grad, layer>(a, cd, t, Lm, SG, lg, s0, tid, nth);
 }
 
 }  // namespace fwi

@@ -11,19 +11,28 @@
 //   step C   Y[r][i] = sum_{(d,q)} F[r][(d,q)] Dhat_d[q][i]  the element's contribution to
 //            K u, scattered into the chunk table as before.
 //
-// Both contractions run as tf32 MMAs with the 3xTF32 split (x = hi + lo, hi = tf32(x);
-// x y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y, accumulated in FP32 in tensor memory), which keeps
-// the product error near FP32's. U (and in gradient steps the forward field) is the A operand
-// in shared memory; Dhat is the B operand in shared memory (loaded once per CTA: the kernel
-// is persistent over chunks); F is the A operand of step C in tensor memory. Tensor memory
-// (256 columns per CTA): G, overwritten by F_hi, at column 0; F_lo at 64; Y at 128; the
-// forward field's G at 160.
+// Both contractions run as tf32 MMAs with the 3xTF32 split: x = hi + lo with hi and lo the
+// nearest tf32 values of x and of x - hi, and x y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y,
+// accumulated in FP32 in tensor memory. The A operands (U, the forward field, F) sit in
+// tensor memory, written row by row by their threads; Dhat is the B operand in shared memory
+// (loaded once per CTA: the kernel is persistent over chunks). Tensor memory, 256 columns
+// per CTA:
+//   [  0,  64)  A of U (hi at 0, lo at 32); after step A: F_lo
+//   [ 64, 128)  A of the forward field (gradient steps; hi at 64, lo at 96); after step A: Y
+//   [128, 192)  G, overwritten by F_hi
+//   [192, 256)  G of the forward field (gradient steps)
+//
+// All global reads of a chunk are issued at once as asynchronous copies (cp.async) into the
+// chunk table: first the values the element phase needs (u, c^2, the forward field), then
+// those only the final update needs (v, the update coefficients, the layer index), whose
+// latency hides behind the element phase.
 //
 // Every wait on the tensor cores is bounded: if one gives up, the CTA sets bit 1 of the
 // status word, stops, frees its tensor memory and returns (the host reports FWI_ETIMEDOUT).
 #pragma once
 #include <cstring>
 
+#include "chunk_io.cuh"
 #include "tc_ptx.cuh"
 
 namespace fwi {
@@ -37,9 +46,9 @@ struct TcShape {
   static constexpr int BA = NG * KA;                            // floats of one B_A image
   static constexpr int BC = NY * NG;                            // floats of one B_C image
   static constexpr int BIMG = 2 * BA + 2 * BC;                  // hi and lo of both
-  static constexpr int AROWS = 128 * KA;                        // floats of one A_U image
-  static constexpr uint32_t COL_G = 0, COL_FLO = 64, COL_Y = 128, COL_GF = 160, COLS = 256;
-  static_assert(NG <= 64 && NY <= 32, "tensor-memory map holds D * NN <= 64, NN <= 32");
+  static constexpr uint32_t COL_AU = 0, COL_FLO = 0, COL_AF = 64, COL_Y = 64, COL_G = 128,
+                            COL_GF = 192, COLS = 256, LO = 32;
+  static_assert(KA <= 32 && NG <= 64 && NY <= 64, "tensor-memory map: NN <= 32, D * NN <= 64");
 };
 
 // Host side: the B images (hi, lo) of Dhat [D][NN][NN] in the canonical K-major layout:
@@ -47,7 +56,7 @@ struct TcShape {
 template <int D, int NN>
 inline void tc_build_bimg(const float* dhat, float* img) {
   typedef TcShape<D, NN> T;
-  auto hi_of = [](float x) {
+  auto tf32 = [](float x) {
     uint32_t u;
     memcpy(&u, &x, 4);
     u = (u + 0x1000u) & 0xFFFFE000u;  // nearest tf32, ties away from zero
@@ -58,41 +67,24 @@ inline void tc_build_bimg(const float* dhat, float* img) {
   for (int i = 0; i < T::BIMG; ++i) img[i] = 0.f;
   for (int n = 0; n < T::NGV; ++n)
     for (int j = 0; j < NN; ++j) {
-      const float x = dhat[n * NN + j], h = hi_of(x);
+      const float x = dhat[n * NN + j], h = tf32(x), l = tf32(x - h);
       img[tc::canon(n, j, T::KA)] = h;
-      img[T::BA + tc::canon(n, j, T::KA)] = x - h;
+      img[T::BA + tc::canon(n, j, T::KA)] = l;
       img[2 * T::BA + tc::canon(j, n, T::NG)] = h;
-      img[2 * T::BA + T::BC + tc::canon(j, n, T::NG)] = x - h;
+      img[2 * T::BA + T::BC + tc::canon(j, n, T::NG)] = l;
     }
 }
 
 // floats of dynamic shared memory of the tensor-core chunk kernel
 template <int D, int NN>
 inline size_t chunk_tc_smem_floats(int L, int SG, bool grad, bool layer) {
-  typedef TcShape<D, NN> T;
-  return (size_t)T::BIMG + (size_t)T::AROWS * (grad ? 4 : 2) + chunk_smem_floats(L, SG, D, grad, layer);
+  return (size_t)TcShape<D, NN>::BIMG + chunk_tab_floats(L, SG, D, grad, layer);
 }
 
-// 3xTF32 GEMM issue (one thread): D[128 x N] = A (shared, hi/lo) x B (shared, hi/lo)^T
-__device__ __forceinline__ void tc_gemm_ss(uint32_t d, const float* ah, const float* al,
-                                           const float* bh, const float* bl, int K, uint32_t idesc) {
-  const uint32_t sbo = (uint32_t)K * 32;
-  uint32_t acc = 0;
-#pragma unroll 1
-  for (int p = 0; p < 3; ++p) {
-    const float* A = p == 2 ? al : ah;
-    const float* B = p == 1 ? bl : bh;
-    const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
-#pragma unroll 1
-    for (int k0 = 0; k0 < K; k0 += 8) {
-      tc::mma_ss(d, tc::sdesc(a0 + k0 * 32, 128, sbo), tc::sdesc(b0 + k0 * 32, 128, sbo), idesc, acc);
-      acc = 1;
-    }
-  }
-}
-// the same with A (hi at column a_hi, lo at a_lo) in tensor memory
-__device__ __forceinline__ void tc_gemm_ts(uint32_t d, uint32_t a_hi, uint32_t a_lo, const float* bh,
-                                           const float* bl, int K, uint32_t idesc) {
+// 3xTF32 GEMM issue (one thread): D[128 x N] = A (tensor memory: hi at a_hi, lo at a_lo)
+// x B (shared, hi/lo images)^T over K
+__device__ __forceinline__ void tc_gemm(uint32_t d, uint32_t a_hi, uint32_t a_lo, const float* bh,
+                                        const float* bl, int K, uint32_t idesc) {
   const uint32_t sbo = (uint32_t)K * 32;
   uint32_t acc = 0;
 #pragma unroll 1
@@ -107,22 +99,20 @@ __device__ __forceinline__ void tc_gemm_ts(uint32_t d, uint32_t a_hi, uint32_t a
   }
 }
 
-// write one row (this thread's) of an A operand image: hi and lo of v[0..KA)
-template <int KA>
-__device__ __forceinline__ void tc_put_row(float* hi, float* lo, int row, const float* v) {
+// this thread's row of an A operand in tensor memory: the hi parts of v[0..K) from address
+// lane_col on, the lo parts lo_off columns further
+template <int K>
+__device__ __forceinline__ void tc_put_row(uint32_t lane_col, uint32_t lo_off, const float* v) {
 #pragma unroll
-  for (int k = 0; k < KA; k += 4) {
-    float4 h, l;
-    h.x = tc::tf32_hi(v[k]);
-    h.y = tc::tf32_hi(v[k + 1]);
-    h.z = tc::tf32_hi(v[k + 2]);
-    h.w = tc::tf32_hi(v[k + 3]);
-    l.x = v[k] - h.x;
-    l.y = v[k + 1] - h.y;
-    l.z = v[k + 2] - h.z;
-    l.w = v[k + 3] - h.w;
-    *reinterpret_cast<float4*>(hi + tc::canon(row, k, KA)) = h;
-    *reinterpret_cast<float4*>(lo + tc::canon(row, k, KA)) = l;
+  for (int k = 0; k < K; k += 8) {
+    float h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = tc::tf32_hi(v[k + i]);
+      l[i] = tc::tf32_hi(v[k + i] - h[i]);
+    }
+    tc::tmem_st8(lane_col + k, h);
+    tc::tmem_st8(lane_col + lo_off + k, l);
   }
 }
 
@@ -145,23 +135,21 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5;
   const int S = a.S, SG = a.SG, s0 = blockIdx.y * SG;
+  const size_t N = (size_t)a.N;
 
   float* Bah = smem;  // B images: B_A hi, lo; B_C hi, lo
   float* Bal = Bah + T::BA;
   float* Bch = Bal + T::BA;
   float* Bcl = Bch + T::BC;
-  float* Auh = Bcl + T::BC;  // A images of U (and of the forward field)
-  float* Aul = Auh + T::AROWS;
-  float* Afh = Aul + T::AROWS;
-  float* Afl = Afh + (grad ? T::AROWS : 0);
-  float* tab = Afl + (grad ? T::AROWS : 0);
   const int Lm = chunk_stride(a.L_max);
-  float* uloc = tab;                       // [SG][Lm]
-  float* yloc = uloc + (size_t)Lm * SG;    // [SG][Lm]
-  float* c2loc = yloc + (size_t)Lm * SG;   // [Lm]
-  float* Floc = c2loc + Lm;                // [SG][Lm] forward field (gradient)
-  float* gloc = Floc + (grad ? (size_t)Lm * SG : 0);  // [Lm]
-  float* sloc = gloc + (grad ? Lm : 0);               // [D*SG][Lm] layer scatter
+  const int lg = __ffs(SG) - 1;
+  const ChunkTab t = chunk_tab(Bcl + T::BC, Lm, SG, D, grad, layer);
+  float* uloc = t.u;
+  float* yloc = t.y;
+  float* c2loc = t.c2;
+  float* Floc = t.F;
+  float* gloc = t.g;
+  float* sloc = t.s;
 
   for (int i = tid; i < T::BIMG / 4; i += nth)
     reinterpret_cast<float4*>(smem)[i] = __ldg(reinterpret_cast<const float4*>(bimg) + i);
@@ -180,40 +168,34 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
   const int el = tid % P, sl = tid / P;
   const int s = s0 + sl;
   for (int c = a.ch0 + (int)blockIdx.x; c < a.ch0 + nrun; c += (int)gridDim.x) {
-    const int* ch = a.chunks + 6 * c;
-    const int e0 = ch[0], ne = ch[1], own_lo = ch[2], own_n = ch[3], nsh = ch[4], hp = ch[5];
-    const int hn = a.chunks[6 * (c + 1) + 5] - hp;
-    const int L = own_n + hn;
+    const ChunkDesc cd = chunk_desc(a, c);
+    const int e0 = cd.e0, ne = cd.ne, nsh = cd.nsh;
 
-    // ---- 1. load the chunk table -------------------------------------------------------
-    for (int i = tid; i < own_n * SG; i += nth) {
-      const int l = i / SG, q = i - l * SG;
-      const size_t g = (size_t)(own_lo + l) * S + s0 + q;
-      uloc[q * Lm + l] = a.u[g];
-      yloc[q * Lm + l] = 0.f;
-      if (grad) Floc[q * Lm + l] = __ldg(a.ring_u + g);
-    }
-    for (int i = tid; i < hn * SG; i += nth) {
-      const int h = i / SG, q = i - h * SG;
-      const size_t g = (size_t)__ldg(a.halo + hp + h) * S + s0 + q;
-      uloc[q * Lm + own_n + h] = a.u[g];
-      yloc[q * Lm + own_n + h] = 0.f;
-      if (grad) Floc[q * Lm + own_n + h] = __ldg(a.ring_u + g);
-    }
-    for (int l = tid; l < L; l += nth) {
-      const int dof = l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n);
-      c2loc[l] = __ldg(a.c2 + dof);
-      if (grad) gloc[l] = 0.f;
-    }
-    if (layer)
-      for (int i = tid; i < Lm * D * SG; i += nth) sloc[i] = 0.f;
-    __syncthreads();
-
-    // ---- 2a. this thread's row of the A operands ----------------------------------------
+    // ---- 1. the chunk's global reads, all in flight at once -------------------------------
+    chunk_load<D, grad, layer>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+    // this thread's element: local connectivity and geometry, read while the copies fly
     const bool valid = el < ne && sl < SG;
     const int e = e0 + el;
     int lq[NS];
     const int lb = nsh + el * NI;
+    float Gm[3] = {0.f, 0.f, 0.f}, Am[D * D];
+#pragma unroll
+    for (int cc = 0; cc < D * D; ++cc) Am[cc] = 0.f;
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < NS; ++q) lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
+#pragma unroll
+      for (int g = 0; g < 3; ++g) Gm[g] = __ldg(a.geo + (size_t)g * a.E + e);
+      if (layer) {
+        const int El = a.E - a.E0;
+#pragma unroll
+        for (int cc = 0; cc < D * D; ++cc) Am[cc] = __ldg(a.lgeo + (size_t)cc * El + (e - a.E0));
+      }
+    }
+    cp_async_wait<1>();  // the element phase's group
+    __syncthreads();
+
+    // ---- 2a. this thread's rows of the A operands -----------------------------------------
     {
       float v[KA];
 #pragma unroll
@@ -221,14 +203,11 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
       if (valid) {
         const float* ur = uloc + sl * Lm;
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
-          v[q] = ur[lq[q]];
-        }
+        for (int q = 0; q < NS; ++q) v[q] = ur[lq[q]];
 #pragma unroll
         for (int j = 0; j < NI; ++j) v[NS + j] = ur[lb + j];
       }
-      tc_put_row<KA>(Auh, Aul, tid, v);
+      tc_put_row<KA>(lane + T::COL_AU, T::LO, v);
       if (grad) {
 #pragma unroll
         for (int k = 0; k < KA; ++k) v[k] = 0.f;
@@ -239,32 +218,21 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
 #pragma unroll
           for (int j = 0; j < NI; ++j) v[NS + j] = fr[lb + j];
         }
-        tc_put_row<KA>(Afh, Afl, tid, v);
+        tc_put_row<KA>(lane + T::COL_AF, T::LO, v);
       }
     }
-    tc::fence_proxy_async();
+    tc::tmem_st_wait();
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      tc_gemm_ss(tmem + T::COL_G, Auh, Aul, Bah, Bal, KA, tc::idesc_tf32(128, NG));
-      if (grad) tc_gemm_ss(tmem + T::COL_GF, Afh, Afl, Bah, Bal, KA, tc::idesc_tf32(128, NG));
+      tc_gemm(tmem + T::COL_G, tmem + T::COL_AU, tmem + T::COL_AU + T::LO, Bah, Bal, KA,
+              tc::idesc_tf32(128, NG));
+      if (grad)
+        tc_gemm(tmem + T::COL_GF, tmem + T::COL_AF, tmem + T::COL_AF + T::LO, Bah, Bal, KA,
+                tc::idesc_tf32(128, NG));
       tc::mma_commit(&bar);
     }
-    // element data while the tensor cores run
-    float Gm[3] = {0.f, 0.f, 0.f}, Am[D * D];
-#pragma unroll
-    for (int cc = 0; cc < D * D; ++cc) Am[cc] = 0.f;
-    if (valid) {
-#pragma unroll
-      for (int g = 0; g < 3; ++g) Gm[g] = __ldg(a.geo + (size_t)g * a.E + e);
-      if (layer) {
-        const int El = a.E - a.E0;
-#pragma unroll
-        for (int cc = 0; cc < D * D; ++cc) Am[cc] = __ldg(a.lgeo + (size_t)cc * El + (e - a.E0));
-      }
-    }
-    auto gdof = [&](int l) { return l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n); };
     {
       const bool ok = tc::mbar_wait(&bar, parity, kTcWaitLimit);
       if (__syncthreads_or(!ok)) {
@@ -297,10 +265,10 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
           if (grad) {
             const float h0 = gfv[q], h1 = gfv[NN + q];
             const float dot = g0 * (Gm[0] * h0 + Gm[1] * h1) + g1 * (Gm[1] * h0 + Gm[2] * h1);
-            atomicAdd(gloc + lqq, 2.f * __ldg(a.cvel + gdof(lqq)) * wq * dot);
+            atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
           }
           if (layer) {
-            const int pi = __ldg(a.pidx + gdof(lqq));
+            const int pi = t.pi[lqq];
             if (pi >= 0) {
               const float* lc = a.lcf + (size_t)pi * LC::COUNT;
               float sq[2], pq[2];
@@ -337,7 +305,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           h[i] = tc::tf32_hi(gv[b + i]);
-          l[i] = gv[b + i] - h[i];
+          l[i] = tc::tf32_hi(gv[b + i] - h[i]);
         }
         tc::tmem_st16(lane + T::COL_G + b, h);
         tc::tmem_st16(lane + T::COL_FLO + b, l);
@@ -348,8 +316,8 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      tc_gemm_ts(tmem + T::COL_Y, tmem + T::COL_G, tmem + T::COL_FLO, Bch, Bcl, NG,
-                 tc::idesc_tf32(128, NY));
+      tc_gemm(tmem + T::COL_Y, tmem + T::COL_G, tmem + T::COL_FLO, Bch, Bcl, NG,
+              tc::idesc_tf32(128, NY));
       tc::mma_commit(&bar);
     }
     {
@@ -405,40 +373,12 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
         for (int j = 0; j < NI; ++j) yr[lb + j] = y[NS + j];
       }
     }
+    cp_async_wait<0>();  // the update's group
     tc::fence_before_sync();
     __syncthreads();
 
     // ---- 3. owned DoFs: final update; halo DoFs: to the global accumulators ----------------
-    for (int i = tid; i < own_n * SG; i += nth) {
-      const int l = i / SG, q = i - l * SG, s2 = s0 + q;
-      float sU[D], sY[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        sU[k] = layer ? sloc[(size_t)(k * SG + q) * Lm + l] : 0.f;
-        sY[k] = 0.f;
-      }
-      dof_update<D>(a, own_lo + l, s2, yloc[q * Lm + l], uloc[q * Lm + l], sU, sY, 0.f);
-    }
-    for (int i = tid; i < hn * SG; i += nth) {
-      const int h = i / SG, q = i - h * SG, s2 = s0 + q;
-      const int dof = __ldg(a.halo + hp + h);
-      const int l = own_n + h;
-      atomicAdd(a.r + (size_t)(dof - a.N_own) * S + s2, yloc[q * Lm + l]);
-      if (layer) {
-        const int pi = __ldg(a.pidx + dof);
-        if (pi >= 0) {
-#pragma unroll
-          for (int k = 0; k < D; ++k)
-            atomicAdd(a.Pacc + ((size_t)pi * D + k) * S + s2, sloc[(size_t)(k * SG + q) * Lm + l]);
-        }
-      }
-    }
-    if (grad) {
-      for (int l = tid; l < L; l += nth) {
-        const int dof = l < own_n ? own_lo + l : __ldg(a.halo + hp + l - own_n);
-        atomicAdd(a.gseg + dof, gloc[l]);
-      }
-    }
+    chunk_store<D, grad, layer>(a, cd, t, Lm, SG, lg, s0, tid, nth);
     __syncthreads();
   }
 
@@ -448,6 +388,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
     if (tid == 0) atomicOr(a.status, 2);
     tc::mbar_wait(&bar, parity, kTcWaitLimit);
   }
+  cp_async_wait<0>();
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {

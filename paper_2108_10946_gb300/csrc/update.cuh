@@ -18,17 +18,15 @@ struct LayerCoef {  // offsets inside one layer DoF's coefficient record
 // plus the layer auxiliaries of the DoF:
 //   forward  P_k' = e1_k P_k - e2f_k sU_k (+ e3f_k sY_k in 3D);  Y' = Y + dt u
 //   adjoint  nu_k' = e1_k nu_k - e2a_k sU_k;  lam_w' = lam_w - dt detPsi1 lam + (dt/M) yw
+// The update with the DoF's v, c1..c3 and layer index already at hand (chunk kernels
+// prefetch them into shared memory).
 template <int D>
-__device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, float y, float uo,
-                                           const float* sU, const float* sY, float yw) {
+__device__ __forceinline__ void dof_update_pre(const StepArgs& a, int dof, int s, float y, float uo,
+                                               float vo, float c1, float c2, float c3, int pi,
+                                               const float* sU, const float* sY, float yw) {
   const int S = a.S;
   const size_t i = (size_t)dof * S + s;
-  const float c1 = __ldg(a.cf + dof);
-  const float c2 = __ldg(a.cf + (size_t)a.N + dof);
-  const float c3 = __ldg(a.cf + 2 * (size_t)a.N + dof);
-  const float vo = a.v[i];
   float vn = c1 * vo - c2 * y - c3 * uo;
-  const int pi = __ldg(a.pidx + dof);
   if (pi >= 0) {
     typedef LayerCoef<D> L;
     const float* lc = a.lcf + (size_t)pi * L::COUNT;
@@ -66,7 +64,20 @@ __device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, fl
   if (!isfinite(un)) atomicOr(a.status, 1);
 }
 
-// Shared-DoF finish: y from the atomic accumulator, then the same update.
+template <int D>
+__device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, float y, float uo,
+                                           const float* sU, const float* sY, float yw) {
+  const float c1 = __ldg(a.cf + dof);
+  const float c2 = __ldg(a.cf + (size_t)a.N + dof);
+  const float c3 = __ldg(a.cf + 2 * (size_t)a.N + dof);
+  const float vo = a.v[(size_t)dof * a.S + s];
+  const int pi = __ldg(a.pidx + dof);
+  dof_update_pre<D>(a, dof, s, y, uo, vo, c1, c2, c3, pi, sU, sY, yw);
+}
+
+// Shared-DoF finish: y from the atomic accumulator, then the same update. Every global
+// read of a thread is issued before its first write (the pointers are declared free of
+// aliasing), so a thread waits for memory once rather than once per dependent access.
 template <int D>
 __global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
   // DoFs [h0, h0 + hcnt): the shared DoFs (plain layout) or the halo DoFs (chunked layout),
@@ -75,39 +86,78 @@ __global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
   const int64_t i = t >> a.log2S;
   const int s = (int)(t & (a.S - 1));
   if (i >= a.hcnt) return;
+  const int S = a.S;
   const int dof = a.h0 + (int)i;
-  const size_t rx = (size_t)i * a.S + s;
-  const size_t ix = (size_t)dof * a.S + s;
-  const float y = a.r[rx];
-  a.r[rx] = 0.f;
-  const float uo = a.u[ix];
-  float sU[D], sY[D];
-  float yw = 0.f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
+  const size_t rx = (size_t)i * S + s;
+  const size_t ix = (size_t)dof * S + s;
+  float* __restrict__ r = a.r;
+  float* __restrict__ u = a.u;
+  float* __restrict__ v = a.v;
+  const float* __restrict__ cf = a.cf;
+  const float y = r[rx];
+  const float uo = u[ix];
+  const float vo = v[ix];
+  const float c1 = __ldg(cf + dof);
+  const float c2 = __ldg(cf + (size_t)a.N + dof);
+  const float c3 = __ldg(cf + 2 * (size_t)a.N + dof);
   const int pi = __ldg(a.pidx + dof);
+  r[rx] = 0.f;
+  float vn = c1 * vo - c2 * y - c3 * uo;
   if (pi >= 0) {
+    typedef LayerCoef<D> L;
+    float* __restrict__ P = a.P;
+    float* __restrict__ Pacc = a.Pacc;
+    const float* __restrict__ lc = a.lcf + (size_t)pi * L::COUNT;
+    float sU[D], sY[D], po[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const size_t pk = ((size_t)pi * D + k) * a.S + s;
-      sU[k] = a.Pacc[pk];
-      a.Pacc[pk] = 0.f;
+      const size_t pk = ((size_t)pi * D + k) * S + s;
+      sU[k] = Pacc[pk];
+      po[k] = P[pk];
+      sY[k] = 0.f;
       if constexpr (D == 3) {
-        if (a.mode == 0) {
-          sY[k] = a.PaccY[pk];
-          a.PaccY[pk] = 0.f;
-        }
+        if (a.mode == 0) sY[k] = a.PaccY[pk];
       }
     }
-    if constexpr (D == 3) {
-      if (a.mode == 1) {
-        const size_t py = (size_t)pi * a.S + s;
-        yw = a.Yacc[py];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const size_t pk = ((size_t)pi * D + k) * S + s;
+      Pacc[pk] = 0.f;
+      if constexpr (D == 3) {
+        if (a.mode == 0) a.PaccY[pk] = 0.f;
+      }
+    }
+    if (a.mode == 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float pn = __ldg(lc + L::E1 + k) * po[k] - __ldg(lc + L::E2F + k) * sU[k];
+        if constexpr (D == 3) pn += __ldg(lc + L::E3F + k) * sY[k];
+        P[((size_t)pi * D + k) * S + s] = pn;
+      }
+      if constexpr (D == 3) {
+        const size_t py = (size_t)pi * S + s;
+        const float yo = a.Y[py];
+        vn -= __ldg(lc + L::C4) * yo;
+        a.Y[py] = yo + a.dt * uo;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        P[((size_t)pi * D + k) * S + s] = __ldg(lc + L::E1 + k) * po[k] - __ldg(lc + L::E2A + k) * sU[k];
+      if constexpr (D == 3) {
+        const size_t py = (size_t)pi * S + s;
+        const float yw = a.Yacc[py];
         a.Yacc[py] = 0.f;
+        const float wo = a.Y[py];
+        vn += __ldg(lc + L::C5) * wo;
+        a.Y[py] = wo - __ldg(lc + L::DTDET) * uo + __ldg(lc + L::DTM) * yw;
       }
     }
   }
-  dof_update<D>(a, dof, s, y, uo, sU, sY, yw);
+  v[ix] = vn;
+  const float un = uo + vn;
+  u[ix] = un;
+  if (!isfinite(un)) atomicOr(a.status, 1);
 }
 
 }  // namespace fwi
