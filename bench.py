@@ -145,6 +145,64 @@ def oracle_rate(wl, nsteps=200, budget_s=15.0):
                 seconds=el)
 
 
+def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0):
+    """A Poisson stream of shot requests over six resident meshes (structured triangle
+    meshes of 20k-180k elements, KMV2..5, 300-step records; a third of the requests carry
+    observed data and ask for the gradient), served twice: by the continuous-batching server
+    (up to 4 shots of one mesh per launch sequence, two workers) and in the one-shot-per-
+    launch form (one worker, one shot per batch). Returns shots/s and p50/p99 latency."""
+    from paper_2108_10946_gb300.serving import Request, ShotServer
+    from synth import meshes, models, signals
+    rng = np.random.default_rng(seed)
+    specs = [(100, 2, 8.0), (140, 3, 6.0), (180, 4, 5.0), (220, 5, 4.0), (260, 3, 3.0),
+             (300, 2, 8.0)]
+    pool = {}
+    for i, (n, k, f) in enumerate(specs):
+        V, C = meshes.structured_tri(n, n, 2.0, 2.0)
+        probe = pkg.Mesh(V, C, k, 1, dt=0.0, cfl_factor=0.8)
+        probe.set_velocity(models.smooth2d(probe.dof_coords() / 2.0))
+        dt = probe.dt
+        probe.close()
+        m = pkg.Mesh(V, C, k, 300, dt=dt, ckpt_stride=30, absorbing=True)
+        m.set_velocity(models.smooth2d(m.dof_coords() / 2.0))
+        recs = np.stack([np.linspace(0.1, 1.9, 50), np.full(50, 1.8)], 1)
+        pool[f"m{i}"] = (m, recs, f)
+    meshes_ = {name: (m, recs) for name, (m, recs, f) in pool.items()}
+    arrivals = np.cumsum(rng.exponential(0.004, nreq))
+    plan = []
+    for i in range(nreq):
+        name = f"m{rng.integers(len(specs))}"
+        m, recs, f = pool[name]
+        wav = signals.ricker_samples(f, m.dt, m.nsteps, t0=1.2 / f)
+        obs = np.zeros((m.nsteps + 1, len(recs)), np.float32) if rng.random() < 1 / 3 else None
+        plan.append((arrivals[i], name, [rng.uniform(0.2, 1.8), rng.uniform(0.1, 0.5)], wav, obs))
+
+    def serve(max_batch, workers):
+        srv = ShotServer(meshes_, hbm_budget_bytes=int(budget_gb * 2 ** 30), max_batch=max_batch,
+                         workers=workers)
+        t0 = time.perf_counter()
+        reqs = []
+        for i, (t, name, src, wav, obs) in enumerate(plan):
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            reqs.append(srv.submit(Request(i, name, src, wav, observed=obs)))
+        for r in reqs:
+            r.event.wait(600)
+        st = srv.stats()
+        srv.close()
+        return st
+
+    serve(4, 2)  # warm-up: resident batches, code paths
+    batched = serve(4, 2)
+    plain = serve(1, 1)
+    for m, _, _ in pool.values():
+        m.close()
+    return {"requests": nreq, "meshes": "6 structured 2D meshes, 20k-180k triangles, KMV2-5",
+            "record_steps": 300, "gradient_fraction": "1/3", "mean_interarrival_s": 0.004,
+            "batched": batched, "one_shot_per_launch": plain}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -333,6 +391,10 @@ def run_ours(args):
         b1.close()
         mp_.close()
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_stream(pkg)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ob = oracle_rate(dict(k=wl["k"], f=wl["f"]))
@@ -360,6 +422,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "plain_form": plain,
+            "serving": serving,
             "clocks": clk_sum,
         }
         print(json.dumps(line), flush=True)
@@ -380,6 +443,7 @@ def main():
     ap.add_argument("--window", type=int, default=2000)
     ap.add_argument("--plain", action="store_true", help="also time the plain form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream latency run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

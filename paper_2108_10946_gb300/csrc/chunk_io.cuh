@@ -9,10 +9,15 @@
 // behind the element phase. Phase 3 (chunk_store) finishes the owned DoFs from the table
 // and sends the halo DoFs' contributions to the global accumulators.
 //
+// Layer chunks of steps without the gradient add a third group (chunk_load_layer, issued
+// once the layer indices are in the table): the damping-layer auxiliaries P (and in the 3D
+// forward Y) of every local layer DoF. Gradient steps, whose table is the largest, read P
+// from global memory instead, so that two CTAs still fit on an SM.
+//
 // Table layout (floats, shot-major [SG][Lm] with Lm odd so that the SG rows of one DoF fall
 // in different banks): u, y, v [SG][Lm]; c2 [Lm]; cf [3][Lm]; pi [Lm] (int); gradient
-// steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm] (and in 3D sY [D][SG][Lm],
-// yw [SG][Lm]).
+// steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm], P [D][SG][Lm] (not in
+// gradient steps) (and in 3D sY [D][SG][Lm], yw [SG][Lm], Yv [SG][Lm]).
 #pragma once
 #include "update.cuh"
 
@@ -38,12 +43,12 @@ __host__ __device__ inline size_t chunk_tab_floats(int L, int SG, int D, bool gr
   const size_t Lm = (size_t)chunk_stride(L);
   size_t f = Lm * (3 * (size_t)SG + 5);
   if (grad) f += Lm * ((size_t)SG + 2);
-  if (layer) f += Lm * D * SG + (D == 3 ? Lm * D * SG + Lm * SG : 0);
+  if (layer) f += (grad ? 1 : 2) * Lm * D * SG + (D == 3 ? Lm * D * SG + 2 * Lm * SG : 0);
   return f;
 }
 
 struct ChunkTab {
-  float *u, *y, *v, *c2, *cf, *F, *g, *cv, *s, *sY, *yw;
+  float *u, *y, *v, *c2, *cf, *F, *g, *cv, *s, *P, *sY, *yw, *Yv;
   int* pi;
 };
 
@@ -63,8 +68,10 @@ __device__ __forceinline__ ChunkTab chunk_tab(float* base, int Lm, int SG, int D
   t.cv = t.g + (grad ? Lm : 0);
   p = t.cv + (grad ? Lm : 0);
   t.s = p;
-  t.sY = t.s + (layer ? (size_t)D * R : 0);
+  t.P = t.s + (layer ? (size_t)D * R : 0);
+  t.sY = t.P + (layer && !grad ? (size_t)D * R : 0);
   t.yw = t.sY + (layer && D == 3 ? (size_t)D * R : 0);
+  t.Yv = t.yw + (layer && D == 3 ? R : 0);
   return t;
 }
 
@@ -139,6 +146,31 @@ __device__ __forceinline__ void chunk_load(const StepArgs& a, const ChunkDesc& c
   }
 }
 
+// Layer chunks, after group 0 has landed and a barrier: the layer auxiliaries of every
+// local layer DoF as a third copy group (P; Y in the 3D forward), zeros elsewhere.
+template <int D>
+__device__ __forceinline__ void chunk_load_layer(const StepArgs& a, const ChunkDesc& cd,
+                                                 const ChunkTab& t, int Lm, int SG, int lg, int s0,
+                                                 int tid, int nth) {
+  const int S = a.S;
+  const bool fwd3 = D == 3 && a.mode == 0;
+  for (int i = tid; i < cd.L * SG; i += nth) {
+    const int l = i >> lg, q = i & (SG - 1);
+    const int pi = t.pi[l];
+    if (pi >= 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        cp_async4(t.P + (size_t)(k * SG + q) * Lm + l, a.P + ((size_t)pi * D + k) * S + s0 + q);
+      if (fwd3) cp_async4(t.Yv + (size_t)q * Lm + l, a.Y + (size_t)pi * S + s0 + q);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) t.P[(size_t)(k * SG + q) * Lm + l] = 0.f;
+      if (fwd3) t.Yv[(size_t)q * Lm + l] = 0.f;
+    }
+  }
+  cp_async_commit();
+}
+
 // Phase 3: owned DoFs final (the increment update from the table), halo DoFs to the
 // global accumulators (finished by the node kernel after all chunks), gradient segment.
 // Call after cp_async_wait<0>() and a barrier.
@@ -161,9 +193,12 @@ __device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& 
       }
       if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
     }
+    float po[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) po[k] = LAYER && !GRAD ? t.P[(size_t)(k * SG + q) * Lm + l] : 0.f;
     dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], t.v[q * Lm + l],
                       t.cf[l], t.cf[Lm + l], t.cf[2 * (size_t)Lm + l], LAYER ? t.pi[l] : -1, sU, sY,
-                      ywv);
+                      ywv, LAYER && !GRAD ? po : nullptr);
   }
   for (int i = tid; i < cd.hn * SG; i += nth) {
     const int h = i >> lg, q = i & (SG - 1), s = s0 + q;

@@ -21,8 +21,12 @@
 namespace fwi {
 
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
-__host__ __device__ inline size_t chunk_smem_floats(int L, int SG, int D, bool grad, bool layer) {
-  return chunk_tab_floats(L, SG, D, grad, layer);
+// (plus, for triangles with NN >= 16, the Dhat rows and the per-thread local connectivity
+// of the rolled per-node loop; nth = threads per CTA)
+__host__ __device__ inline size_t chunk_smem_floats(int L, int SG, int D, bool grad, bool layer,
+                                                    int NN = 0, int NS = 0, int nth = 0) {
+  const size_t roll = D == 2 && NN >= 16 ? (size_t)D * NN * ((NN + 3) / 4 * 4) + (size_t)NS * nth : 0;
+  return ((chunk_tab_floats(L, SG, D, grad, layer) + 3) & ~size_t(3)) + roll;
 }
 
 // MODE: 0 forward, 1 adjoint, 2 adjoint with the gradient integrand; LAYER: the chunk's
@@ -31,6 +35,11 @@ template <int D, int NN, int NS, int MODE, bool LAYER>
 __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   constexpr int NI = NN - NS;
   constexpr int NG = D == 2 ? 3 : 6;
+  // triangles with NN >= 16: the per-node loop stays rolled, with the rows of Dhat read from shared memory,
+  // so that the kernel's code fits the instruction cache; smaller elements unroll it fully
+  // with Dhat as constant-bank operands
+  constexpr bool ROLL = D == 2 && NN >= 16;
+  constexpr int NNP = (NN + 3) / 4 * 4;
   typedef LayerCoef<D> LC;
   const int c = blockIdx.x + a.ch0;
   const int* ch = a.chunks + 6 * c;
@@ -59,10 +68,26 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   cd.e0 = e0, cd.ne = ne, cd.own_lo = own_lo, cd.own_n = own_n, cd.nsh = nsh, cd.hp = hp;
   cd.hn = hn, cd.L = own_n + hn;
 
+  // rolled form: Dhat rows [D][NN][NNP] and the element's shared-node local indices
+  // [NS][nth] after the chunk table
+  float* dhs = smem + ((chunk_tab_floats(a.L_max, SG, D, grad, layer) + 3) & ~size_t(3));
+  int* lqs = reinterpret_cast<int*>(dhs + (ROLL ? (size_t)D * NN * NNP : 0));
+
   // ---- 1. load -------------------------------------------------------------------------
   chunk_load<D, grad, layer>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+  if constexpr (ROLL) {
+    for (int i = tid; i < D * NN * NNP; i += nth) {
+      const int r = i / NNP, j = i - r * NNP;
+      dhs[i] = j < NN ? c_dhat[r * NN + j] : 0.f;
+    }
+  }
   cp_async_wait<1>();
   __syncthreads();
+  if (layer && !grad) {
+    chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+    cp_async_wait<0>();
+    __syncthreads();
+  }
 
   // ---- 2. elements ---------------------------------------------------------------------
   const int P = a.PE;
@@ -73,7 +98,10 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     const int s = s0 + sl;
     int lq[NS];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
+    for (int q = 0; q < NS; ++q) {
+      lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
+      if constexpr (ROLL) lqs[q * nth + tid] = lq[q];
+    }
     const int lb = nsh + el * NI;  // local index of the first bubble node
     float U[NN], F[NN];
     const float* ur = uloc + sl * Lm;
@@ -103,8 +131,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
       if (layer && !adj) {
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
-          const int pi = piloc[q < NS ? lq[q] : lb + q - NS];
-          Yv[q] = pi >= 0 ? a.Y[(size_t)pi * S + s] : 0.f;
+          Yv[q] = t.Yv[(size_t)sl * Lm + (q < NS ? lq[q] : lb + q - NS)];
         }
       }
     }
@@ -112,6 +139,136 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
 #pragma unroll
     for (int i = 0; i < NN; ++i) y[i] = yw[i] = 0.f;
 
+if constexpr (ROLL) {
+#pragma unroll 1
+    for (int q = 0; q < NN; ++q) {
+      const int lqq = q < NS ? lqs[q * nth + tid] : lb + (q - NS);
+      float row[D][NNP];  // Dhat[d][q][:] for every d, 16-byte loads from shared memory
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int j = 0; j < NNP; j += 4) {
+          const float4 r4 = *reinterpret_cast<const float4*>(dhs + ((size_t)d * NN + q) * NNP + j);
+          row[d][j] = r4.x;
+          row[d][j + 1] = r4.y;
+          row[d][j + 2] = r4.z;
+          row[d][j + 3] = r4.w;
+        }
+      float g[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        float a0 = 0.f, a1 = 0.f;  // two partial sums: shorter dependent FMA chains
+#pragma unroll
+        for (int j = 0; j < NN; j += 2) a0 = fmaf(row[d][j], U[j], a0);
+#pragma unroll
+        for (int j = 1; j < NN; j += 2) a1 = fmaf(row[d][j], U[j], a1);
+        g[d] = a0 + a1;
+      }
+      const float wq = c_w[q];  // uniform dynamic index
+      const float wc = wq * c2loc[lqq];
+      float f[D];
+      if constexpr (D == 2) {
+        f[0] = wc * (G[0] * g[0] + G[1] * g[1]);
+        f[1] = wc * (G[1] * g[0] + G[2] * g[1]);
+      } else {
+        f[0] = wc * (G[0] * g[0] + G[1] * g[1] + G[2] * g[2]);
+        f[1] = wc * (G[1] * g[0] + G[3] * g[1] + G[4] * g[2]);
+        f[2] = wc * (G[2] * g[0] + G[4] * g[1] + G[5] * g[2]);
+      }
+      if (grad) {
+        float gf[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+          for (int j = 0; j < NN; j += 2) a0 = fmaf(row[d][j], F[j], a0);
+#pragma unroll
+          for (int j = 1; j < NN; j += 2) a1 = fmaf(row[d][j], F[j], a1);
+          gf[d] = a0 + a1;
+        }
+        float dot;
+        if constexpr (D == 2) {
+          dot = g[0] * (G[0] * gf[0] + G[1] * gf[1]) + g[1] * (G[1] * gf[0] + G[2] * gf[1]);
+        } else {
+          dot = g[0] * (G[0] * gf[0] + G[1] * gf[1] + G[2] * gf[2]) +
+                g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
+                g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
+        }
+        atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
+      }
+      if (layer) {
+        const int pi = piloc[lqq];
+        if (pi >= 0) {
+          const float* lc = a.lcf + (size_t)pi * LC::COUNT;
+          float sq[D], pq[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
+            sq[k] = wq * acc;
+            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
+          }
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc += Am[d * D + k] * pq[k];
+            f[d] += wq * acc;
+          }
+          float sY[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) sY[k] = 0.f;
+          if constexpr (D == 3) {
+            if (adj) {
+              float pw[3], fw[3];
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
+                        __ldg(lc + LC::PSI3 + k);
+#pragma unroll
+              for (int d = 0; d < 3; ++d)
+                fw[d] = wq * (Am[d * 3 + 0] * pw[0] + Am[d * 3 + 1] * pw[1] + Am[d * 3 + 2] * pw[2]);
+#pragma unroll
+              for (int i = 0; i < NN; ++i)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) yw[i] = fmaf(row[d][i], fw[d], yw[i]);
+            } else {
+              float gy[3];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < NN; ++j) acc = fmaf(row[d][j], Yv[j], acc);
+                gy[d] = acc;
+              }
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                sY[k] = wq * (Am[0 * 3 + k] * gy[0] + Am[1 * 3 + k] * gy[1] + Am[2 * 3 + k] * gy[2]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float* sp = sloc + (size_t)(k * SG + sl) * Lm + lqq;
+            float* syp = sYloc + (size_t)(k * SG + sl) * Lm + lqq;
+            if (q < NS) {
+              atomicAdd(sp, sq[k]);
+              if constexpr (D == 3) atomicAdd(syp, sY[k]);
+            } else {
+              *sp = sq[k];
+              if constexpr (D == 3) *syp = sY[k];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NN; ++i)
+#pragma unroll
+        for (int d = 0; d < D; ++d) y[i] = fmaf(row[d][i], f[d], y[i]);
+    }
+
+    } else {
 #pragma unroll
     for (int q = 0; q < NN; ++q) {
       const int lqq = q < NS ? lq[q] : lb + (q - NS);
@@ -168,7 +325,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = a.P[((size_t)pi * D + k) * S + s];
+            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -186,7 +343,8 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = a.P[((size_t)pi * 3 + k) * S + s] * __ldg(lc + LC::PSI3 + k);
+                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
+                        __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)
                 fw[d] = wq * (Am[d * 3 + 0] * pw[0] + Am[d * 3 + 1] * pw[1] + Am[d * 3 + 2] * pw[2]);
@@ -228,6 +386,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
         for (int d = 0; d < D; ++d) y[i] = fmaf(c_dhat[(d * NN + q) * NN + i], f[d], y[i]);
     }
 
+    }
     // sources and receivers of this element (flagged elements only)
     const int slot = __ldg(a.inj + e);
     if (slot >= 0) {

@@ -194,6 +194,11 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
     }
     cp_async_wait<1>();  // the element phase's group
     __syncthreads();
+    if (layer && !grad) {
+      chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+      cp_async_wait<0>();
+      __syncthreads();
+    }
 
     // ---- 2a. this thread's rows of the A operands -----------------------------------------
     {
@@ -275,7 +280,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
                 sq[k] = wq * (Am[0 * 2 + k] * g0 + Am[1 * 2 + k] * g1);
-                const float raw = a.P[((size_t)pi * 2 + k) * S + s];
+                const float raw = grad ? a.P[((size_t)pi * 2 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
                 pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
               }
               f0 += wq * (Am[0] * pq[0] + Am[1] * pq[1]);

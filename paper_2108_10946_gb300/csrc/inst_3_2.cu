@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(128) k_chunk(const StepArgs a) {
 template <int MODE, bool LAYER>
 int launch_chunk_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   if (nch <= 0) return 0;
-  const size_t bytes = chunk_smem_floats(a.L_max, a.SG, D, MODE == 2, LAYER) * sizeof(float);
+  const size_t bytes =
+      chunk_smem_floats(a.L_max, a.SG, D, MODE == 2, LAYER, NN, NS, a.PE * a.SG) * sizeof(float);
   if (bytes > 227 * 1024) return (int)cudaErrorInvalidValue;
   static size_t configured[64] = {0};
   int dev = 0;

@@ -23,7 +23,8 @@ struct LayerCoef {  // offsets inside one layer DoF's coefficient record
 template <int D>
 __device__ __forceinline__ void dof_update_pre(const StepArgs& a, int dof, int s, float y, float uo,
                                                float vo, float c1, float c2, float c3, int pi,
-                                               const float* sU, const float* sY, float yw) {
+                                               const float* sU, const float* sY, float yw,
+                                               const float* po = nullptr) {
   const int S = a.S;
   const size_t i = (size_t)dof * S + s;
   float vn = c1 * vo - c2 * y - c3 * uo;
@@ -34,7 +35,8 @@ __device__ __forceinline__ void dof_update_pre(const StepArgs& a, int dof, int s
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const size_t pk = ((size_t)pi * D + k) * S + s;
-        float pn = __ldg(lc + L::E1 + k) * a.P[pk] - __ldg(lc + L::E2F + k) * sU[k];
+        const float pold = po ? po[k] : a.P[pk];
+        float pn = __ldg(lc + L::E1 + k) * pold - __ldg(lc + L::E2F + k) * sU[k];
         if constexpr (D == 3) pn += __ldg(lc + L::E3F + k) * sY[k];
         a.P[pk] = pn;
       }
@@ -48,7 +50,8 @@ __device__ __forceinline__ void dof_update_pre(const StepArgs& a, int dof, int s
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const size_t pk = ((size_t)pi * D + k) * S + s;
-        a.P[pk] = __ldg(lc + L::E1 + k) * a.P[pk] - __ldg(lc + L::E2A + k) * sU[k];
+        const float pold = po ? po[k] : a.P[pk];
+        a.P[pk] = __ldg(lc + L::E1 + k) * pold - __ldg(lc + L::E2A + k) * sU[k];
       }
       if constexpr (D == 3) {
         const size_t py = (size_t)pi * S + s;

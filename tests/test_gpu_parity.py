@@ -196,3 +196,58 @@ def test_forward_and_gradient_3d_layer(lib, k, layout):
     gerr = rel_l2(o["G_gpu"], o["G_orc"])
     print(f"3D k={k} layout={layout}: gradient rel-L2 = {gerr:.3e}")
     assert gerr < GRAD_TOL
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_shot_batch_of_four_matches_two_batches_of_two(lib, dim):
+    """Batches whose shot count is a multiple of 4 finish the halo DoFs with one thread per
+    DoF and float4 shot groups; smaller batches with one thread per (DoF, shot). The same
+    four shots as one batch of 4 and as two batches of 2 (damping layer, absorbing boundary,
+    gradient) must agree to FP32 summation-order noise."""
+    if dim == 2:
+        V, C, lay = _case2d(3, n=10, layer=True)
+        k, cfun = 3, models.smooth2d
+        srcs = np.array([[0.5, 0.1], [0.2, 0.15], [0.8, 0.2], [0.35, 0.3]])
+        recs = np.array([[x, 0.9] for x in np.linspace(0.05, 0.95, 9)])
+    else:
+        g = np.linspace(0.0, 1.0, 6)
+        V, C = meshes.kuhn_tets(g, g, np.linspace(0.0, 0.8, 5))
+        lay = dict(box=[(0.2, 0.8), (0.2, 0.8), (-10.0, 0.6)], faces=0b101111, width=0.2,
+                   smax=signals.sigma_max(2.2, 0.2))
+        k, cfun = 2, models.smooth3d
+        srcs = np.array([[0.5, 0.5, 0.1], [0.4, 0.55, 0.15], [0.6, 0.45, 0.2], [0.45, 0.4, 0.12]])
+        recs = np.array([[x, y, 0.5] for x in (0.3, 0.5, 0.7) for y in (0.35, 0.65)])
+    box = [tuple(b) for b in lay["box"]]
+    mesh = lib.Mesh(V, C, k, 1, dt=0.0, cfl_factor=0.8, box=box, layer_faces=lay["faces"],
+                    layer_width=lay["width"], sigma_max=lay["smax"], absorbing=True)
+    mesh.set_velocity(cfun(mesh.dof_coords()))
+    dt = mesh.dt
+    mesh.close()
+    nt = int(round(0.5 / dt))
+    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=True, ckpt_stride=13, box=box,
+                    layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"])
+    mesh.set_velocity(cfun(mesh.dof_coords()))
+    wav = np.stack([signals.ricker_samples(8.0, dt, nt, t0=0.15) * (1 + 0.1 * i) for i in range(4)])
+    wav_d = torch.from_numpy(wav).float().cuda()
+
+    def run(sel):
+        b = lib.Batch(mesh, srcs[sel], recs)
+        rec = torch.zeros((len(sel), nt + 1, len(recs)), device="cuda")
+        b.forward(wav_d[sel].contiguous(), rec)
+        b.adjoint((0.1 * rec).contiguous())
+        G = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+        b.gradient_raw(G)
+        b.close()
+        return rec.cpu().numpy(), G.cpu().numpy()
+
+    r4, g4 = run([0, 1, 2, 3])
+    ra, ga = run([0, 1])
+    rb, gb = run([2, 3])
+    r2 = np.concatenate([ra, rb])
+    for s in range(4):
+        err = rel_l2(r4[s], r2[s])
+        print(f"dim={dim} shot {s}: batch of 4 vs batches of 2, records rel-L2 = {err:.3e}")
+        assert err < 1e-6
+    gerr = rel_l2(g4, ga + gb)
+    print(f"dim={dim}: gradient rel-L2 = {gerr:.3e}")
+    assert gerr < 1e-6
