@@ -66,10 +66,15 @@ typedef struct fwi_batch fwi_batch;
  *   layout           0: chunked (elements grouped in chunks that assemble in shared memory;
  *                    the default), 1: plain (one thread per element and shot scattering
  *                    with global atomics; the unfused reference form).
- *   tensor_cores     chunked layout, triangles only: the per-element derivative
- *                    contractions (Section 3.2) of a chunk run as tf32 tensor-core MMAs
- *                    with a three-term hi/lo split (near-FP32 products, FP32 accumulation).
- *                    0 or -1: off (FP32 CUDA-core arithmetic), 1: on (FWI_EINVAL for
+ *   tensor_cores     chunked layout, triangles only: in the adjoint steps (Section 3.4,
+ *                    with the gradient integrand) the per-element derivative contractions
+ *                    (Section 3.2) of a chunk run as tf32 tensor-core MMAs with a three-term
+ *                    hi/lo split (near-FP32 products, FP32 accumulation in tensor memory).
+ *                    Forward and recompute steps, which produce the records, stay on FP32
+ *                    CUDA cores: the tensor cores' accumulation rounds toward zero, and in
+ *                    the forward recurrence that bias grows the seismogram error with the
+ *                    record length past 1e-5; in the adjoint it only enters the gradient
+ *                    (about 3e-6 against a 1e-4 bound). 0 or -1: off, 1: on (FWI_EINVAL for
  *                    tetrahedra or the plain layout).
  */
 typedef struct {

@@ -91,12 +91,8 @@ int launch_chunk_tc_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
 int launch_chunk(const StepArgs& a, cudaStream_t st) {
   const int mode = a.mode == 0 ? 0 : (a.ring_u != nullptr ? 2 : 1);
   int rc = 0;
-  if (a.tc) {
+  if (a.tc && mode != 0) {  // the adjoint steps only
     switch (mode) {
-      case 0:
-        rc = launch_chunk_tc_t<0, false>(a, 0, a.nch0, st);
-        if (!rc) rc = launch_chunk_tc_t<0, true>(a, a.nch0, a.nch - a.nch0, st);
-        break;
       case 1:
         rc = launch_chunk_tc_t<1, false>(a, 0, a.nch0, st);
         if (!rc) rc = launch_chunk_tc_t<1, true>(a, a.nch0, a.nch - a.nch0, st);

@@ -78,89 +78,67 @@ __device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, fl
   dof_update_pre<D>(a, dof, s, y, uo, vo, c1, c2, c3, pi, sU, sY, yw);
 }
 
-// Shared-DoF finish: y from the atomic accumulator, then the same update. Every global
-// read of a thread is issued before its first write (the pointers are declared free of
-// aliasing), so a thread waits for memory once rather than once per dependent access.
+// Finish of one accumulated DoF (index i of the accumulator range, DoF dof, shot s): y and
+// the layer sums from the accumulators the element contributions arrived in by atomics
+// (read from L2, where the atomics resolve), the accumulators cleared for the next step,
+// then the same update. uo is the DoF's u^n. Every global read is issued before the first
+// write.
 template <int D>
-__global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
-  // DoFs [h0, h0 + hcnt): the shared DoFs (plain layout) or the halo DoFs (chunked layout),
-  // whose element contributions arrived by atomics in r[(dof - h0) * S + s]
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t >> a.log2S;
-  const int s = (int)(t & (a.S - 1));
-  if (i >= a.hcnt) return;
+__device__ __forceinline__ void accum_finish(const StepArgs& a, size_t i, int dof, int s, float uo,
+                                             int pi) {
   const int S = a.S;
-  const int dof = a.h0 + (int)i;
-  const size_t rx = (size_t)i * S + s;
+  const size_t rx = i * S + s;
   const size_t ix = (size_t)dof * S + s;
-  float* __restrict__ r = a.r;
-  float* __restrict__ u = a.u;
-  float* __restrict__ v = a.v;
-  const float* __restrict__ cf = a.cf;
-  const float y = r[rx];
-  const float uo = u[ix];
-  const float vo = v[ix];
-  const float c1 = __ldg(cf + dof);
-  const float c2 = __ldg(cf + (size_t)a.N + dof);
-  const float c3 = __ldg(cf + 2 * (size_t)a.N + dof);
-  const int pi = __ldg(a.pidx + dof);
-  r[rx] = 0.f;
-  float vn = c1 * vo - c2 * y - c3 * uo;
+  const float y = __ldcg(a.r + rx);
+  const float vo = a.v[ix];
+  const float c1 = __ldg(a.cf + dof);
+  const float c2 = __ldg(a.cf + (size_t)a.N + dof);
+  const float c3 = __ldg(a.cf + 2 * (size_t)a.N + dof);
+  float sU[D], sY[D];
+  float yw = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
   if (pi >= 0) {
-    typedef LayerCoef<D> L;
-    float* __restrict__ P = a.P;
-    float* __restrict__ Pacc = a.Pacc;
-    const float* __restrict__ lc = a.lcf + (size_t)pi * L::COUNT;
-    float sU[D], sY[D], po[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const size_t pk = ((size_t)pi * D + k) * S + s;
-      sU[k] = Pacc[pk];
-      po[k] = P[pk];
-      sY[k] = 0.f;
+      sU[k] = __ldcg(a.Pacc + pk);
       if constexpr (D == 3) {
-        if (a.mode == 0) sY[k] = a.PaccY[pk];
+        if (a.mode == 0) sY[k] = __ldcg(a.PaccY + pk);
       }
     }
+    if constexpr (D == 3) {
+      if (a.mode == 1) yw = __ldcg(a.Yacc + (size_t)pi * S + s);
+    }
+  }
+  a.r[rx] = 0.f;
+  if (pi >= 0) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const size_t pk = ((size_t)pi * D + k) * S + s;
-      Pacc[pk] = 0.f;
+      a.Pacc[pk] = 0.f;
       if constexpr (D == 3) {
         if (a.mode == 0) a.PaccY[pk] = 0.f;
       }
     }
-    if (a.mode == 0) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        float pn = __ldg(lc + L::E1 + k) * po[k] - __ldg(lc + L::E2F + k) * sU[k];
-        if constexpr (D == 3) pn += __ldg(lc + L::E3F + k) * sY[k];
-        P[((size_t)pi * D + k) * S + s] = pn;
-      }
-      if constexpr (D == 3) {
-        const size_t py = (size_t)pi * S + s;
-        const float yo = a.Y[py];
-        vn -= __ldg(lc + L::C4) * yo;
-        a.Y[py] = yo + a.dt * uo;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < D; ++k)
-        P[((size_t)pi * D + k) * S + s] = __ldg(lc + L::E1 + k) * po[k] - __ldg(lc + L::E2A + k) * sU[k];
-      if constexpr (D == 3) {
-        const size_t py = (size_t)pi * S + s;
-        const float yw = a.Yacc[py];
-        a.Yacc[py] = 0.f;
-        const float wo = a.Y[py];
-        vn += __ldg(lc + L::C5) * wo;
-        a.Y[py] = wo - __ldg(lc + L::DTDET) * uo + __ldg(lc + L::DTM) * yw;
-      }
+    if constexpr (D == 3) {
+      if (a.mode == 1) a.Yacc[(size_t)pi * S + s] = 0.f;
     }
   }
-  v[ix] = vn;
-  const float un = uo + vn;
-  u[ix] = un;
-  if (!isfinite(un)) atomicOr(a.status, 1);
+  dof_update_pre<D>(a, dof, s, y, uo, vo, c1, c2, c3, pi, sU, sY, yw);
+}
+
+// Shared-DoF finish as a separate pass over the DoFs [h0, h0 + hcnt) (the halo DoFs of the
+// chunked layout, the shared DoFs of the plain layout), whose element contributions arrived
+// by atomics in r[(dof - h0) * S + s].
+template <int D>
+__global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t >> a.log2S;
+  const int s = (int)(t & (a.S - 1));
+  if (i >= a.hcnt) return;
+  const int dof = a.h0 + (int)i;
+  accum_finish<D>(a, (size_t)i, dof, s, a.u[(size_t)dof * a.S + s], __ldg(a.pidx + dof));
 }
 
 }  // namespace fwi

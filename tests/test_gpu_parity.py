@@ -87,11 +87,11 @@ def _run_both(lib, V, C, k, lay, T, srcs, recs, absorbing, grad=False, cfun=mode
     return out
 
 
-@pytest.mark.parametrize("form", [SIMT, TC, PLAIN], ids=["chunked", "chunked-tc", "plain"])
+@pytest.mark.parametrize("form", [SIMT, PLAIN], ids=["chunked", "plain"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_forward_records_2d(lib, k, form):
-    """Every form of the step: chunked shared-memory assembly with FP32 CUDA-core or
-    tensor-core contractions, and plain global atomics."""
+    """Both data layouts of the forward step: chunked shared-memory assembly and plain
+    global atomics."""
     V, C, lay = _case2d(k)
     srcs = [[0.5, 0.3], [0.31, 0.62]]
     recs = [[x, 0.85] for x in np.linspace(0.05, 0.95, 9)]
@@ -127,9 +127,10 @@ def test_forward_and_gradient_2d_layer(lib, k, form):
 @pytest.mark.parametrize("k", [4, 5])
 def test_tensor_core_step_matches_cuda_core_step(lib, k, S):
     """Shot counts the oracle cases above do not reach (one shot per CTA row group, a full
-    128-row tile, two shot groups per chunk): the tensor-core step against the FP32 CUDA-core
-    step (itself held to the oracle above), records and gradient, with a damping layer, an
-    absorbing boundary and chunks that straddle the layer."""
+    128-row tile, two shot groups per chunk), with a damping layer, an absorbing boundary and
+    chunks that straddle the layer: with tensor_cores = 1 the records are those of the FP32
+    CUDA-core forward (the same kernels), and the gradient from the tensor-core adjoint
+    matches the CUDA-core one (itself held to the oracle above) within the gradient bound."""
     V, C, lay = _case2d(k, n=14, layer=True)
     dt = 0.8 * OracleCase(V, C, k, models.smooth2d, 1.0, 1, layer=lay, absorbing=True).ops.cfl_dt()
     nt = int(round(0.6 / dt))
@@ -157,10 +158,10 @@ def test_tensor_core_step_matches_cuda_core_step(lib, k, S):
         mesh.close()
     (rc, Gc, xc), (rt, Gt, xt) = out["cuda"], out["tc"]
     assert np.array_equal(xc, xt)
-    for s in range(S):
+    for s in range(S):  # same kernels; only the order of shared-memory atomics differs
         err = rel_l2(rt[s], rc[s])
-        print(f"k={k} S={S} shot {s}: tensor-core vs CUDA-core records rel-L2 = {err:.3e}")
-        assert err < REC_TOL
+        print(f"k={k} S={S} shot {s}: records rel-L2 = {err:.3e}")
+        assert err < 1e-6
     gerr = rel_l2(Gt, Gc)
     print(f"k={k} S={S}: tensor-core vs CUDA-core gradient rel-L2 = {gerr:.3e}")
     assert gerr < GRAD_TOL
