@@ -14,8 +14,12 @@
 // forward Y) of every local layer DoF. Gradient steps, whose table is the largest, read P
 // from global memory instead, so that two CTAs still fit on an SM.
 //
+// Layer chunks (two to four times the table of the others) skip group 1 and read v and
+// c1..c3 from global memory in phase 3, which keeps two of their CTAs on an SM.
+//
 // Table layout (floats, shot-major [SG][Lm] with Lm odd so that the SG rows of one DoF fall
-// in different banks): u, y, v [SG][Lm]; c2 [Lm]; cf [3][Lm]; pi [Lm] (int); gradient
+// in different banks): u, y [SG][Lm]; c2 [Lm]; pi [Lm] (int); v [SG][Lm] and cf [3][Lm]
+// (not in layer chunks); gradient
 // steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm], P [D][SG][Lm] (not in
 // gradient steps) (and in 3D sY [D][SG][Lm], yw [SG][Lm], Yv [SG][Lm]).
 #pragma once
@@ -41,7 +45,7 @@ __host__ __device__ inline int chunk_stride(int L) { return L | 1; }
 
 __host__ __device__ inline size_t chunk_tab_floats(int L, int SG, int D, bool grad, bool layer) {
   const size_t Lm = (size_t)chunk_stride(L);
-  size_t f = Lm * (3 * (size_t)SG + 5);
+  size_t f = Lm * (2 * (size_t)SG + 2) + (layer ? 0 : Lm * ((size_t)SG + 3));
   if (grad) f += Lm * ((size_t)SG + 2);
   if (layer) f += (grad ? 1 : 2) * Lm * D * SG + (D == 3 ? Lm * D * SG + 2 * Lm * SG : 0);
   return f;
@@ -58,11 +62,12 @@ __device__ __forceinline__ ChunkTab chunk_tab(float* base, int Lm, int SG, int D
   const size_t R = (size_t)Lm * SG;
   t.u = base;
   t.y = t.u + R;
-  t.v = t.y + R;
-  t.c2 = t.v + R;
-  t.cf = t.c2 + Lm;
-  t.pi = reinterpret_cast<int*>(t.cf + 3 * (size_t)Lm);
-  float* p = reinterpret_cast<float*>(t.pi + Lm);
+  t.c2 = t.y + R;
+  t.pi = reinterpret_cast<int*>(t.c2 + Lm);
+  t.v = reinterpret_cast<float*>(t.pi + Lm);  // v and cf: not in layer chunks (see above)
+  t.cf = t.v + (layer ? 0 : R);
+  float* p0 = t.cf + (layer ? 0 : 3 * (size_t)Lm);
+  float* p = p0;
   t.F = p;
   t.g = t.F + (grad ? R : 0);
   t.cv = t.g + (grad ? Lm : 0);
@@ -119,17 +124,19 @@ __device__ __forceinline__ void chunk_load(const StepArgs& a, const ChunkDesc& c
     if (GRAD) cp_async4(t.cv + l, a.cvel + dof);
   }
   cp_async_commit();
-  for (int i = tid; i < cd.own_n * SG; i += nth) {
-    const int l = i >> lg, q = i & (SG - 1);
-    cp_async4(t.v + q * Lm + l, a.v + (size_t)(cd.own_lo + l) * S + s0 + q);
+  if (!LAYER) {
+    for (int i = tid; i < cd.own_n * SG; i += nth) {
+      const int l = i >> lg, q = i & (SG - 1);
+      cp_async4(t.v + q * Lm + l, a.v + (size_t)(cd.own_lo + l) * S + s0 + q);
+    }
+    for (int l = tid; l < cd.own_n; l += nth) {
+      const size_t dof = (size_t)(cd.own_lo + l);
+      cp_async4(t.cf + l, a.cf + dof);
+      cp_async4(t.cf + Lm + l, a.cf + N + dof);
+      cp_async4(t.cf + 2 * (size_t)Lm + l, a.cf + 2 * N + dof);
+    }
   }
-  for (int l = tid; l < cd.own_n; l += nth) {
-    const size_t dof = (size_t)(cd.own_lo + l);
-    cp_async4(t.cf + l, a.cf + dof);
-    cp_async4(t.cf + Lm + l, a.cf + N + dof);
-    cp_async4(t.cf + 2 * (size_t)Lm + l, a.cf + 2 * N + dof);
-  }
-  cp_async_commit();
+  cp_async_commit();  // (empty for layer chunks: the group count stays the same)
   for (int i = tid; i < cd.L * SG; i += nth) {
     const int l = i >> lg, q = i & (SG - 1);
     t.y[q * Lm + l] = 0.f;
@@ -193,12 +200,20 @@ __device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& 
       }
       if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
     }
-    float po[D];
+    if (LAYER) {
+      // layer chunks keep their table small (two CTAs per SM): v and c1..c3 from global
+      const int dof = cd.own_lo + l;
+      float po[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) po[k] = LAYER && !GRAD ? t.P[(size_t)(k * SG + q) * Lm + l] : 0.f;
-    dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], t.v[q * Lm + l],
-                      t.cf[l], t.cf[Lm + l], t.cf[2 * (size_t)Lm + l], LAYER ? t.pi[l] : -1, sU, sY,
-                      ywv, LAYER && !GRAD ? po : nullptr);
+      for (int k = 0; k < D; ++k) po[k] = GRAD ? 0.f : t.P[(size_t)(k * SG + q) * Lm + l];
+      dof_update_pre<D>(a, dof, s, t.y[q * Lm + l], t.u[q * Lm + l], a.v[(size_t)dof * S + s],
+                        __ldg(a.cf + dof), __ldg(a.cf + (size_t)a.N + dof),
+                        __ldg(a.cf + 2 * (size_t)a.N + dof), t.pi[l], sU, sY, ywv,
+                        GRAD ? nullptr : po);
+    } else {
+      dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], t.v[q * Lm + l],
+                        t.cf[l], t.cf[Lm + l], t.cf[2 * (size_t)Lm + l], -1, sU, sY, ywv);
+    }
   }
   for (int i = tid; i < cd.hn * SG; i += nth) {
     const int h = i >> lg, q = i & (SG - 1), s = s0 + q;

@@ -20,6 +20,18 @@
 
 namespace fwi {
 
+// d = a * b + c on two FP32 lanes at once (packed FP32x2 FMA of the sm_100 family; each
+// lane an IEEE fused multiply-add rounded to nearest)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&r);
+}
+
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
 // (plus, for triangles with NN >= 16, the Dhat rows and the per-thread local connectivity
 // of the rolled per-node loop; nth = threads per CTA)
@@ -39,6 +51,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   // so that the kernel's code fits the instruction cache; smaller elements unroll it fully
   // with Dhat as constant-bank operands
   constexpr bool ROLL = D == 2 && NN >= 16;
+  static_assert(!ROLL || NN % 2 == 0, "the rolled form pairs nodes for packed FMAs");
   constexpr int NNP = (NN + 3) / 4 * 4;
   typedef LayerCoef<D> LC;
   const int c = blockIdx.x + a.ch0;
@@ -157,12 +170,13 @@ if constexpr (ROLL) {
       float g[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        float a0 = 0.f, a1 = 0.f;  // two partial sums: shorter dependent FMA chains
+        // (even j, odd j) partial sums in one packed FP32x2 FMA: each half is an FP32 fused
+        // multiply-add, so the sums equal the two scalar chains of the unrolled form
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < NN; j += 2) a0 = fmaf(row[d][j], U[j], a0);
-#pragma unroll
-        for (int j = 1; j < NN; j += 2) a1 = fmaf(row[d][j], U[j], a1);
-        g[d] = a0 + a1;
+        for (int j = 0; j < NN; j += 2)
+          acc = ffma2(make_float2(row[d][j], row[d][j + 1]), make_float2(U[j], U[j + 1]), acc);
+        g[d] = acc.x + acc.y;
       }
       const float wq = c_w[q];  // uniform dynamic index
       const float wc = wq * c2loc[lqq];
@@ -179,12 +193,11 @@ if constexpr (ROLL) {
         float gf[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          float a0 = 0.f, a1 = 0.f;
+          float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < NN; j += 2) a0 = fmaf(row[d][j], F[j], a0);
-#pragma unroll
-          for (int j = 1; j < NN; j += 2) a1 = fmaf(row[d][j], F[j], a1);
-          gf[d] = a0 + a1;
+          for (int j = 0; j < NN; j += 2)
+            acc = ffma2(make_float2(row[d][j], row[d][j + 1]), make_float2(F[j], F[j + 1]), acc);
+          gf[d] = acc.x + acc.y;
         }
         float dot;
         if constexpr (D == 2) {
@@ -263,9 +276,14 @@ if constexpr (ROLL) {
         }
       }
 #pragma unroll
-      for (int i = 0; i < NN; ++i)
+      for (int i = 0; i < NN; i += 2) {  // y[i], y[i+1] in one packed FMA per d
+        float2 yy = make_float2(y[i], y[i + 1]);
 #pragma unroll
-        for (int d = 0; d < D; ++d) y[i] = fmaf(row[d][i], f[d], y[i]);
+        for (int d = 0; d < D; ++d)
+          yy = ffma2(make_float2(row[d][i], row[d][i + 1]), make_float2(f[d], f[d]), yy);
+        y[i] = yy.x;
+        y[i + 1] = yy.y;
+      }
     }
 
     } else {
