@@ -26,9 +26,9 @@ const KernelSet* kernel_set(int dim, int k) {
 
 void launch_node_update(const StepArgs& a, int dim, cudaStream_t st) {
   const int bs = 256;
-  const int64_t threads = (int64_t)a.hcnt * a.S;
-  if (threads == 0) return;
-  const unsigned blocks = (unsigned)((threads + bs - 1) / bs);
+  const int64_t items = (int64_t)a.hcnt * a.S;
+  if (items == 0) return;
+  const unsigned blocks = (unsigned)((items + (int64_t)bs * NODE_ITEMS - 1) / ((int64_t)bs * NODE_ITEMS));
   if (dim == 2)
     node_kernel<2><<<blocks, bs, 0, st>>>(a);
   else

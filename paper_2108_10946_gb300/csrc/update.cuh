@@ -78,6 +78,8 @@ __device__ __forceinline__ void dof_update(const StepArgs& a, int dof, int s, fl
   dof_update_pre<D>(a, dof, s, y, uo, vo, c1, c2, c3, pi, sU, sY, yw);
 }
 
+constexpr int NODE_ITEMS = 4;
+
 // Finish of one accumulated DoF (index i of the accumulator range, DoF dof, shot s): y and
 // the layer sums from the accumulators the element contributions arrived in by atomics
 // (read from L2, where the atomics resolve), the accumulators cleared for the next step,
@@ -133,12 +135,68 @@ __device__ __forceinline__ void accum_finish(const StepArgs& a, size_t i, int do
 // by atomics in r[(dof - h0) * S + s].
 template <int D>
 __global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t >> a.log2S;
-  const int s = (int)(t & (a.S - 1));
-  if (i >= a.hcnt) return;
-  const int dof = a.h0 + (int)i;
-  accum_finish<D>(a, (size_t)i, dof, s, a.u[(size_t)dof * a.S + s], __ldg(a.pidx + dof));
+  // NODE_ITEMS (DoF, shot) items per thread, a block-stride apart (coalesced); all their
+  // reads are issued before any write, so that each thread has NODE_ITEMS times more
+  // memory requests in flight
+  const int S = a.S;
+  const int64_t total = (int64_t)a.hcnt << a.log2S;
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * NODE_ITEMS + threadIdx.x;
+  float uo[NODE_ITEMS], vo[NODE_ITEMS], y[NODE_ITEMS], c1[NODE_ITEMS], c2[NODE_ITEMS],
+      c3[NODE_ITEMS];
+  int pi[NODE_ITEMS];
+#pragma unroll
+  for (int k = 0; k < NODE_ITEMS; ++k) {
+    const int64_t t = base + (int64_t)k * blockDim.x;
+    uo[k] = vo[k] = y[k] = c1[k] = c2[k] = c3[k] = 0.f;
+    pi[k] = -1;
+    if (t < total) {
+      const int64_t i = t >> a.log2S;
+      const int dof = a.h0 + (int)i;
+      const size_t ix = (size_t)dof * S + (t & (S - 1));
+      uo[k] = a.u[ix];
+      vo[k] = a.v[ix];
+      y[k] = __ldcg(a.r + (size_t)t);
+      c1[k] = __ldg(a.cf + dof);
+      c2[k] = __ldg(a.cf + (size_t)a.N + dof);
+      c3[k] = __ldg(a.cf + 2 * (size_t)a.N + dof);
+      pi[k] = __ldg(a.pidx + dof);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NODE_ITEMS; ++k) {
+    const int64_t t = base + (int64_t)k * blockDim.x;
+    if (t >= total) continue;
+    const int64_t i = t >> a.log2S;
+    const int dof = a.h0 + (int)i;
+    const int s = (int)(t & (S - 1));
+    a.r[(size_t)t] = 0.f;
+    float sU[D], sY[D];
+    float yw = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) sU[d] = sY[d] = 0.f;
+    if (pi[k] >= 0) {  // damping layer: the layer sums (a minority of the DoFs)
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const size_t pk = ((size_t)pi[k] * D + d) * S + s;
+        sU[d] = __ldcg(a.Pacc + pk);
+        a.Pacc[pk] = 0.f;
+        if constexpr (D == 3) {
+          if (a.mode == 0) {
+            sY[d] = __ldcg(a.PaccY + pk);
+            a.PaccY[pk] = 0.f;
+          }
+        }
+      }
+      if constexpr (D == 3) {
+        if (a.mode == 1) {
+          const size_t py = (size_t)pi[k] * S + s;
+          yw = __ldcg(a.Yacc + py);
+          a.Yacc[py] = 0.f;
+        }
+      }
+    }
+    dof_update_pre<D>(a, dof, s, y[k], uo[k], vo[k], c1[k], c2[k], c3[k], pi[k], sU, sY, yw);
+  }
 }
 
 }  // namespace fwi
