@@ -186,33 +186,50 @@ __device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& 
                                             int Lm, int SG, int lg, int s0, int tid, int nth) {
   const int S = a.S;
   const bool adj = a.mode != 0;
-  for (int i = tid; i < cd.own_n * SG; i += nth) {
-    const int l = i >> lg, q = i & (SG - 1), s = s0 + q;
-    float sU[D], sY[D];
-    float ywv = 0.f;
+  if (LAYER) {
+    // layer chunks read v and c1..c3 from global memory: four items per round, their reads
+    // issued before any write
+    for (int i0 = tid; i0 < cd.own_n * SG; i0 += 4 * nth) {
+      float vo[4], c1[4], c2[4], c3[4];
 #pragma unroll
-    for (int k = 0; k < D; ++k) sU[k] = sY[k] = 0.f;
-    if (LAYER) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        sU[k] = t.s[(size_t)(k * SG + q) * Lm + l];
-        if constexpr (D == 3) sY[k] = t.sY[(size_t)(k * SG + q) * Lm + l];
+      for (int k = 0; k < 4; ++k) {
+        const int i = i0 + k * nth;
+        vo[k] = c1[k] = c2[k] = c3[k] = 0.f;
+        if (i < cd.own_n * SG) {
+          const int l = i >> lg, dof = cd.own_lo + l;
+          vo[k] = a.v[(size_t)dof * S + s0 + (i & (SG - 1))];
+          c1[k] = __ldg(a.cf + dof);
+          c2[k] = __ldg(a.cf + (size_t)a.N + dof);
+          c3[k] = __ldg(a.cf + 2 * (size_t)a.N + dof);
+        }
       }
-      if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
-    }
-    if (LAYER) {
-      // layer chunks keep their table small (two CTAs per SM): v and c1..c3 from global
-      const int dof = cd.own_lo + l;
-      float po[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) po[k] = GRAD ? 0.f : t.P[(size_t)(k * SG + q) * Lm + l];
-      dof_update_pre<D>(a, dof, s, t.y[q * Lm + l], t.u[q * Lm + l], a.v[(size_t)dof * S + s],
-                        __ldg(a.cf + dof), __ldg(a.cf + (size_t)a.N + dof),
-                        __ldg(a.cf + 2 * (size_t)a.N + dof), t.pi[l], sU, sY, ywv,
-                        GRAD ? nullptr : po);
-    } else {
+      for (int k = 0; k < 4; ++k) {
+        const int i = i0 + k * nth;
+        if (i >= cd.own_n * SG) break;
+        const int l = i >> lg, q = i & (SG - 1), s = s0 + q;
+        float sU[D], sY[D], po[D];
+        float ywv = 0.f;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          sU[d] = t.s[(size_t)(d * SG + q) * Lm + l];
+          sY[d] = 0.f;
+          if constexpr (D == 3) sY[d] = t.sY[(size_t)(d * SG + q) * Lm + l];
+          po[d] = GRAD ? 0.f : t.P[(size_t)(d * SG + q) * Lm + l];
+        }
+        if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
+        dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], vo[k], c1[k], c2[k],
+                          c3[k], t.pi[l], sU, sY, ywv, GRAD ? nullptr : po);
+      }
+    }
+  } else {
+    for (int i = tid; i < cd.own_n * SG; i += nth) {
+      const int l = i >> lg, q = i & (SG - 1), s = s0 + q;
+      float sU[D], sY[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) sU[d] = sY[d] = 0.f;
       dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], t.v[q * Lm + l],
-                        t.cf[l], t.cf[Lm + l], t.cf[2 * (size_t)Lm + l], -1, sU, sY, ywv);
+                        t.cf[l], t.cf[Lm + l], t.cf[2 * (size_t)Lm + l], -1, sU, sY, 0.f);
     }
   }
   for (int i = tid; i < cd.hn * SG; i += nth) {

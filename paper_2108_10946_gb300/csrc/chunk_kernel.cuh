@@ -170,13 +170,17 @@ if constexpr (ROLL) {
       float g[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        // (even j, odd j) partial sums in one packed FP32x2 FMA: each half is an FP32 fused
-        // multiply-add, so the sums equal the two scalar chains of the unrolled form
-        float2 acc = make_float2(0.f, 0.f);
+        // four partial sums (j mod 4) in two packed FP32x2 FMA chains: shorter dependent
+        // chains for the few warps an SM holds
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < NN; j += 2)
-          acc = ffma2(make_float2(row[d][j], row[d][j + 1]), make_float2(U[j], U[j + 1]), acc);
-        g[d] = acc.x + acc.y;
+        for (int j = 0; j < NN; j += 4) {
+          acc0 = ffma2(make_float2(row[d][j], row[d][j + 1]), make_float2(U[j], U[j + 1]), acc0);
+          if (j + 2 < NN)
+            acc1 = ffma2(make_float2(row[d][j + 2], row[d][j + 3]),
+                         make_float2(U[j + 2], j + 3 < NN ? U[j + 3] : 0.f), acc1);
+        }
+        g[d] = (acc0.x + acc1.x) + (acc0.y + acc1.y);
       }
       const float wq = c_w[q];  // uniform dynamic index
       const float wc = wq * c2loc[lqq];
@@ -193,11 +197,15 @@ if constexpr (ROLL) {
         float gf[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          float2 acc = make_float2(0.f, 0.f);
+          float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < NN; j += 2)
-            acc = ffma2(make_float2(row[d][j], row[d][j + 1]), make_float2(F[j], F[j + 1]), acc);
-          gf[d] = acc.x + acc.y;
+          for (int j = 0; j < NN; j += 4) {
+            acc0 = ffma2(make_float2(row[d][j], row[d][j + 1]), make_float2(F[j], F[j + 1]), acc0);
+            if (j + 2 < NN)
+              acc1 = ffma2(make_float2(row[d][j + 2], row[d][j + 3]),
+                           make_float2(F[j + 2], j + 3 < NN ? F[j + 3] : 0.f), acc1);
+          }
+          gf[d] = (acc0.x + acc1.x) + (acc0.y + acc1.y);
         }
         float dot;
         if constexpr (D == 2) {
