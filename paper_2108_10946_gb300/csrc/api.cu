@@ -175,6 +175,8 @@ struct fwi_batch {
   float* gseg = nullptr;
   double *gsum = nullptr, *gcomp = nullptr, *misfit = nullptr;
   int* status = nullptr;
+  cudaStream_t st2 = nullptr;  // second stream of the chunked step (layer chunks)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // staging for host pointers
   float* wav_dev = nullptr;  // [S][nt] the forward's wavelet, re-injected by the recompute
   float* rec_dev = nullptr;  // [S][nt+1][R] the forward's records
@@ -1006,6 +1008,9 @@ int fwi_get_dt(const fwi_mesh* m, double* dt) {
 int fwi_batch_free(fwi_batch* b) {
   if (!b) return 0;
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->st2) cudaStreamDestroy(b->st2);
   void* ptrs[] = {b->d_inj, b->d_src_elem, b->d_src_phi, b->d_rslot_ptr, b->d_rslot_rec,
                   b->d_rslot_phi, b->d_rec_elem, b->d_rec_phi, b->u, b->v, b->r, b->P, b->Pacc,
                   b->PaccY, b->Y, b->Yacc, b->ua, b->va, b->Pa, b->Ya, b->ckpt, b->ring,
@@ -1081,6 +1086,11 @@ int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const
       (rc = dalloc(&b->gsum, (size_t)N)) || (rc = dalloc(&b->gcomp, (size_t)N)) ||
       (rc = dalloc(&b->misfit, 1)) || (rc = dalloc(&b->status, 1)))
     return rc;
+  if (m->layout == 0) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  }
   CUDA_TRY(cudaMemset(b->r, 0, NS_ * sizeof(float)));
   if (LS) {
     CUDA_TRY(cudaMemset(b->Pacc, 0, LS * sizeof(float)));
@@ -1171,7 +1181,18 @@ void run_step(fwi_batch* b, const StepArgs& a, cudaStream_t st) {
   }
   if (e) cudaEventRecord(e[0], st);
   if (b->m->layout == 0) {
-    int rc = b->m->ks->launch_chunk(a, st);
+    // the layer chunks run on a second stream, concurrently with the others (disjoint owned
+    // DoFs; halo sums by atomics); the node kernel waits for both
+    const bool fork = b->st2 && b->m->nch0 > 0 && b->m->nch() > b->m->nch0;
+    if (fork) {
+      cudaEventRecord(b->ev_fork, st);
+      cudaStreamWaitEvent(b->st2, b->ev_fork, 0);
+    }
+    int rc = b->m->ks->launch_chunk(a, st, fork ? b->st2 : st);
+    if (fork) {
+      cudaEventRecord(b->ev_join, b->st2);
+      cudaStreamWaitEvent(st, b->ev_join, 0);
+    }
     if (rc) b->launch_error = rc;
   } else {
     b->m->ks->launch_step(a, st);

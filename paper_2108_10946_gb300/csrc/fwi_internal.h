@@ -81,7 +81,9 @@ struct KernelSet {
   int dim, k, nn, ns, ni;
   int (*upload_constants)(const float* dhat, const float* w);  // [D][NN][NN], [NN]
   void (*launch_step)(const StepArgs& a, cudaStream_t st);        // plain layout
-  int (*launch_chunk)(const StepArgs& a, cudaStream_t st);        // chunked layout
+  // chunked layout: chunks without layer elements on st, layer chunks on st_layer (the two
+  // launches are independent and may overlap; st_layer may be st)
+  int (*launch_chunk)(const StepArgs& a, cudaStream_t st, cudaStream_t st_layer);
   void (*launch_record)(const StepArgs& a, const int* rec_elem, const float* rec_phi,
                         cudaStream_t st);  // d^n for every receiver and shot
 };

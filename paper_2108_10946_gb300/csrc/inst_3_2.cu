@@ -45,21 +45,21 @@ int launch_chunk_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
 }
 
 // chunks [0, nch0) hold no damping-layer element, chunks [nch0, nch) do
-int launch_chunk(const StepArgs& a, cudaStream_t st) {
+int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
   const int mode = a.mode == 0 ? 0 : (a.ring_u != nullptr ? 2 : 1);
   int rc = 0;
   switch (mode) {
     case 0:
       rc = launch_chunk_t<0, false>(a, 0, a.nch0, st);
-      if (!rc) rc = launch_chunk_t<0, true>(a, a.nch0, a.nch - a.nch0, st);
+      if (!rc) rc = launch_chunk_t<0, true>(a, a.nch0, a.nch - a.nch0, stl);
       break;
     case 1:
       rc = launch_chunk_t<1, false>(a, 0, a.nch0, st);
-      if (!rc) rc = launch_chunk_t<1, true>(a, a.nch0, a.nch - a.nch0, st);
+      if (!rc) rc = launch_chunk_t<1, true>(a, a.nch0, a.nch - a.nch0, stl);
       break;
     default:
       rc = launch_chunk_t<2, false>(a, 0, a.nch0, st);
-      if (!rc) rc = launch_chunk_t<2, true>(a, a.nch0, a.nch - a.nch0, st);
+      if (!rc) rc = launch_chunk_t<2, true>(a, a.nch0, a.nch - a.nch0, stl);
   }
   return rc;
 }
