@@ -441,7 +441,8 @@ def main():
     ap.add_argument("--shots", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=50)
     ap.add_argument("--window", type=int, default=2000)
-    ap.add_argument("--plain", action="store_true", help="also time the plain form")
+    ap.add_argument("--no-plain", dest="plain", action="store_false",
+                    help="skip timing the plain form (one shot per launch, plain layout)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream latency run")
     args = ap.parse_args()
