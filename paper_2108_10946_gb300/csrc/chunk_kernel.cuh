@@ -33,11 +33,12 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 }
 
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
-// (plus, for triangles with NN >= 16, the Dhat rows and the per-thread local connectivity
-// of the rolled per-node loop; nth = threads per CTA)
+// (plus, for the rolled per-node loop, the per-thread local connectivity and, for triangles
+// with NN >= 16, the Dhat rows; nth = threads per CTA)
 __host__ __device__ inline size_t chunk_smem_floats(int L, int SG, int D, bool grad, bool layer,
                                                     int NN = 0, int NS = 0, int nth = 0) {
-  const size_t roll = D == 2 && NN >= 16 ? (size_t)D * NN * ((NN + 3) / 4 * 4) + (size_t)NS * nth : 0;
+  const size_t roll = D == 2 && NN >= 16 ? (size_t)D * NN * ((NN + 3) / 4 * 4) + (size_t)NS * nth
+                      : D == 3 && NN >= 32 ? (size_t)NS * nth : 0;
   return ((chunk_tab_floats(L, SG, D, grad, layer) + 3) & ~size_t(3)) + roll;
 }
 
@@ -51,6 +52,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   // so that the kernel's code fits the instruction cache; smaller elements unroll it fully
   // with Dhat as constant-bank operands
   constexpr bool ROLL = D == 2 && NN >= 16;
+  constexpr bool ROLL3 = D == 3 && NN >= 32;  // KMV3 tetrahedra (measured: KMV2 tets lose)
   static_assert(!ROLL || NN % 2 == 0, "the rolled form pairs nodes for packed FMAs");
   constexpr int NNP = (NN + 3) / 4 * 4;
   typedef LayerCoef<D> LC;
@@ -113,7 +115,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
-      if constexpr (ROLL) lqs[q * nth + tid] = lq[q];
+      if constexpr (ROLL || ROLL3) lqs[q * nth + tid] = lq[q];
     }
     const int lb = nsh + el * NI;  // local index of the first bubble node
     float U[NN], F[NN];
@@ -294,7 +296,127 @@ if constexpr (ROLL) {
       }
     }
 
-    } else {
+    } else if constexpr (ROLL3) {
+      // KMV3 tetrahedra: the per-node loop rolled, Dhat from the constant bank with a
+      // warp-uniform dynamic index (the unrolled loop does not fit the instruction cache)
+#pragma unroll 1
+    for (int q = 0; q < NN; ++q) {
+      const int lqq = q < NS ? lqs[q * nth + tid] : lb + (q - NS);
+      float g[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        float a0 = 0.f, a1 = 0.f;  // two partial sums: shorter dependent FMA chains
+#pragma unroll
+        for (int j = 0; j < NN; j += 2) a0 = fmaf(c_dhat[(d * NN + q) * NN + j], U[j], a0);
+#pragma unroll
+        for (int j = 1; j < NN; j += 2) a1 = fmaf(c_dhat[(d * NN + q) * NN + j], U[j], a1);
+        g[d] = a0 + a1;
+      }
+      const float wq = c_w[q];
+      const float wc = wq * c2loc[lqq];
+      float f[D];
+      if constexpr (D == 2) {
+        f[0] = wc * (G[0] * g[0] + G[1] * g[1]);
+        f[1] = wc * (G[1] * g[0] + G[2] * g[1]);
+      } else {
+        f[0] = wc * (G[0] * g[0] + G[1] * g[1] + G[2] * g[2]);
+        f[1] = wc * (G[1] * g[0] + G[3] * g[1] + G[4] * g[2]);
+        f[2] = wc * (G[2] * g[0] + G[4] * g[1] + G[5] * g[2]);
+      }
+      if (grad) {
+        float gf[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+          for (int j = 0; j < NN; j += 2) a0 = fmaf(c_dhat[(d * NN + q) * NN + j], F[j], a0);
+#pragma unroll
+          for (int j = 1; j < NN; j += 2) a1 = fmaf(c_dhat[(d * NN + q) * NN + j], F[j], a1);
+          gf[d] = a0 + a1;
+        }
+        float dot;
+        if constexpr (D == 2) {
+          dot = g[0] * (G[0] * gf[0] + G[1] * gf[1]) + g[1] * (G[1] * gf[0] + G[2] * gf[1]);
+        } else {
+          dot = g[0] * (G[0] * gf[0] + G[1] * gf[1] + G[2] * gf[2]) +
+                g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
+                g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
+        }
+        atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
+      }
+      if (layer) {
+        const int pi = piloc[lqq];
+        if (pi >= 0) {
+          const float* lc = a.lcf + (size_t)pi * LC::COUNT;
+          float sq[D], pq[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
+            sq[k] = wq * acc;
+            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
+          }
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc += Am[d * D + k] * pq[k];
+            f[d] += wq * acc;
+          }
+          float sY[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) sY[k] = 0.f;
+          if constexpr (D == 3) {
+            if (adj) {
+              float pw[3], fw[3];
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
+                        __ldg(lc + LC::PSI3 + k);
+#pragma unroll
+              for (int d = 0; d < 3; ++d)
+                fw[d] = wq * (Am[d * 3 + 0] * pw[0] + Am[d * 3 + 1] * pw[1] + Am[d * 3 + 2] * pw[2]);
+#pragma unroll
+              for (int i = 0; i < NN; ++i)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) yw[i] = fmaf(c_dhat[(d * NN + q) * NN + i], fw[d], yw[i]);
+            } else {
+              float gy[3];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < NN; ++j) acc = fmaf(c_dhat[(d * NN + q) * NN + j], Yv[j], acc);
+                gy[d] = acc;
+              }
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                sY[k] = wq * (Am[0 * 3 + k] * gy[0] + Am[1 * 3 + k] * gy[1] + Am[2 * 3 + k] * gy[2]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float* sp = sloc + (size_t)(k * SG + sl) * Lm + lqq;
+            float* syp = sYloc + (size_t)(k * SG + sl) * Lm + lqq;
+            if (q < NS) {
+              atomicAdd(sp, sq[k]);
+              if constexpr (D == 3) atomicAdd(syp, sY[k]);
+            } else {
+              *sp = sq[k];
+              if constexpr (D == 3) *syp = sY[k];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NN; ++i)
+#pragma unroll
+        for (int d = 0; d < D; ++d) y[i] = fmaf(c_dhat[(d * NN + q) * NN + i], f[d], y[i]);
+    }
+
+        } else {
 #pragma unroll
     for (int q = 0; q < NN; ++q) {
       const int lqq = q < NS ? lq[q] : lb + (q - NS);
