@@ -20,6 +20,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -295,8 +296,7 @@ def run_ours(args):
         dist.barrier()
     pkg.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    clk = Clocks(os.path.join(args.clocks_dir, f"clocks_rank{rank}.csv"))
     with clk:
         torch.cuda.synchronize()
         ev0.record()
@@ -444,6 +444,8 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false",
                     help="skip timing the plain form (one shot per launch, plain layout)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream latency run")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -157,9 +157,12 @@ int fwi_batch_set_sources(fwi_batch* b, const double* src);
  * admission test of a memory-budgeted shot server. */
 int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes);
 
-/* Forward solve, Eq. (forward3) with the readings documented in the design doc, for every shot
- * of the batch. wavelet[S][Nt] floats (w(t_n), n = 0..Nt-1); rec_out[S][Nt+1][R] floats
- * (d^n = H U^n). Stores the checkpoints the adjoint needs. */
+/* Forward solve, Eq. (forward3), for every shot of the batch: central differences in time,
+ * the damping-layer auxiliaries of Section 2.1 staggered half a step (their damping taken
+ * Crank-Nicolson: the paper's own layer scheme is not legible), in the increment form
+ * v' = c1 v - c2 K u - c3 u, u' = u + v'. wavelet[S][Nt] floats (w(t_n),
+ * n = 0..Nt-1); rec_out[S][Nt+1][R] floats (d^n = H U^n). Stores the checkpoints the
+ * adjoint needs. */
 int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
 
 /* Allocation-free variant of fwi_forward_shot (the paper has no counterpart: this is a
