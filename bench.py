@@ -32,6 +32,13 @@ PEAK_HBM_FALLBACK = 6800.0
 SM_COUNT, FP32_LANES = 152, 128
 
 
+METRIC = "DoF-steps/s (forward + adjoint, FP32, <=1e-5 rel-L2 vs FP64 oracle)"
+
+
+def workload_name(k):
+    return f"marine2d-17x3.5km-kmv{k}-layer1km-5Hz-4s"
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -222,11 +229,13 @@ def run_reference(args):
     v = float(np.mean(vals))
     sample = (f"FP64 oracle, KMV{wl_k}tri window of the marine model (2 km x 1.5 km, "
               f"{last['E']} elements, N={last['N']}), {last['nsteps']} forward + adjoint steps per rep")
-    line = {"impl": "reference", "metric": "DoF-steps/s (forward + adjoint)", "value": v,
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * el / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"marine2d-kmv{wl_k}-window", "model": "oracle"},
+            "config": {"workload": workload_name(wl_k),
+                       "sample": "the FP64 oracle on one host core, timed on a bounded window of "
+                                 "the workload (see cpu_baseline.sample)"},
             "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -404,11 +413,11 @@ def run_ours(args):
                           f"steps x {ob['reps']}, {ob['seconds']:.1f} s")}
     if rank == 0:
         line = {
-            "metric": "DoF-steps/s (forward + adjoint, FP32, <=1e-5 rel-L2 vs FP64 oracle)",
+            "metric": METRIC,
             "value": value, "unit": "DoF-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"marine2d-17x3.5km-kmv{wl['k']}-layer1km-5Hz-4s",
+            "config": {"workload": workload_name(wl["k"]),
                        "elements": E, "dofs": N, "dt": dt, "record_steps": nt_record,
                        "window_steps": nt, "shots_per_step": S,
                        "receivers": R, "ckpt_stride": args.ckpt, "C": wl["C"],
