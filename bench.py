@@ -153,12 +153,13 @@ def oracle_rate(wl, nsteps=200, budget_s=15.0):
                 seconds=el)
 
 
-def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0):
-    """A Poisson stream of shot requests over six resident meshes (structured triangle
-    meshes of 20k-180k elements, KMV2..5, 300-step records; a third of the requests carry
-    observed data and ask for the gradient), served twice: by the continuous-batching server
-    (up to 4 shots of one mesh per launch sequence, two workers) and in the one-shot-per-
-    launch form (one worker, one shot per batch). Returns shots/s and p50/p99 latency."""
+def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0, interarrivals=(0.008, 0.004, 0.002)):
+    """Poisson streams of shot requests over six resident meshes (structured triangle meshes
+    of 20k-180k elements, KMV2..5, 300-step records; half of the requests carry observed data
+    and ask for the gradient), at three mean inter-arrival times. Each stream is served twice:
+    by the continuous-batching server (up to 4 shots of one mesh per launch sequence, two
+    workers) and in the one-shot-per-launch form (one worker, one shot per batch). Returns
+    shots/s and p50/p99 latency per stream."""
     from paper_2108_10946_gb300.serving import Request, ShotServer
     from synth import meshes, models, signals
     rng = np.random.default_rng(seed)
@@ -176,16 +177,19 @@ def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0):
         recs = np.stack([np.linspace(0.1, 1.9, 50), np.full(50, 1.8)], 1)
         pool[f"m{i}"] = (m, recs, f)
     meshes_ = {name: (m, recs) for name, (m, recs, f) in pool.items()}
-    arrivals = np.cumsum(rng.exponential(0.004, nreq))
-    plan = []
-    for i in range(nreq):
-        name = f"m{rng.integers(len(specs))}"
-        m, recs, f = pool[name]
-        wav = signals.ricker_samples(f, m.dt, m.nsteps, t0=1.2 / f)
-        obs = np.zeros((m.nsteps + 1, len(recs)), np.float32) if rng.random() < 1 / 3 else None
-        plan.append((arrivals[i], name, [rng.uniform(0.2, 1.8), rng.uniform(0.1, 0.5)], wav, obs))
 
-    def serve(max_batch, workers):
+    def make_plan(mean_gap):
+        arrivals = np.cumsum(rng.exponential(mean_gap, nreq))
+        plan = []
+        for i in range(nreq):
+            name = f"m{rng.integers(len(specs))}"
+            m, recs, f = pool[name]
+            wav = signals.ricker_samples(f, m.dt, m.nsteps, t0=1.2 / f)
+            obs = np.zeros((m.nsteps + 1, len(recs)), np.float32) if rng.random() < 0.5 else None
+            plan.append((arrivals[i], name, [rng.uniform(0.2, 1.8), rng.uniform(0.1, 0.5)], wav, obs))
+        return plan
+
+    def serve(plan, max_batch, workers):
         srv = ShotServer(meshes_, hbm_budget_bytes=int(budget_gb * 2 ** 30), max_batch=max_batch,
                          workers=workers)
         t0 = time.perf_counter()
@@ -201,14 +205,17 @@ def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0):
         srv.close()
         return st
 
-    serve(4, 2)  # warm-up: resident batches, code paths
-    batched = serve(4, 2)
-    plain = serve(1, 1)
+    serve(make_plan(interarrivals[0]), 4, 2)  # warm-up: resident batches, code paths
+    streams = []
+    for gap in interarrivals:
+        plan = make_plan(gap)
+        streams.append({"mean_interarrival_s": gap, "batched": serve(plan, 4, 2),
+                        "one_shot_per_launch": serve(plan, 1, 1)})
     for m, _, _ in pool.values():
         m.close()
-    return {"requests": nreq, "meshes": "6 structured 2D meshes, 20k-180k triangles, KMV2-5",
-            "record_steps": 300, "gradient_fraction": "1/3", "mean_interarrival_s": 0.004,
-            "batched": batched, "one_shot_per_launch": plain}
+    return {"requests_per_stream": nreq,
+            "meshes": "6 structured 2D meshes, 20k-180k triangles, KMV2-5",
+            "record_steps": 300, "gradient_fraction": "1/2", "streams": streams}
 
 
 def run_reference(args):
