@@ -17,9 +17,9 @@ Modules:
             gradient3), misfit (Eq. l2error), CFL estimate (Eq. spectral)
   analytic  Ricker wavelet and the 2D free-space Green's function image sum
 
-Parity status: every function is pinned by tests under tests/test_oracle_*.py, except
-the KMV4tri/KMV5tri node positions (the paper does not print them; they are solved here
-from the moment equations), whose agreement with the paper's own tables is "parity
-unpinned", and the damping-layer time scheme (the printed block matrices are garbled;
-see wave.py), whose agreement with the paper's exact scheme is "parity unpinned".
+Parity status: every function is pinned by tests under tests/test_oracle_*.py. The
+KMV4tri/KMV5tri nodes (not printed in the paper; solved here from the moment equations at
+degree k + k' - 2) are pinned by their convergence order, not by a table. The
+damping-layer time scheme (the printed block matrices are garbled; see wave.py) is "parity
+unpinned" against the paper's exact scheme.
 """

@@ -8,8 +8,10 @@ and integrating the mass matrix with that rule makes it diagonal.
   * Node positions: KMV2tri and KMV3tri from Fig. 2dels, KMV2tet and KMV3tet from
     Fig. 3dels. The paper does not print KMV4tri / KMV5tri nodes; here they are solved
     from the symmetric moment equations (Newton from a coarse start, then checked for
-    positivity, inclusion and unisolvence). Their agreement with the paper's own elements
-    is "parity unpinned".
+    positivity, inclusion and unisolvence) at the degree k + k' - 2 of the classical
+    mass-lumping condition (7 and 10). Their node positions are not compared with the
+    paper's own tables; their accuracy is pinned instead by the convergence order k + 1
+    of a manufactured solution (tests/test_oracle_wave.py).
   * Weights: one weight per symmetry orbit, solved from the moment equations (exact
     integration of monomials up to the highest degree the nodes admit).
   * Space: P_k plus bubbles (b = product of barycentrics):
@@ -302,19 +304,17 @@ def newton_orbit_rule(kinds, params0, D, iters=60):
 # are readings (the paper does not list these elements' nodes):
 #   KMV4tri: vertices, edge midpoints, one edge pair, two interior 3-orbits; the degree-7
 #     equations have a unique solution.
-#   KMV5tri: vertices, two edge pairs, three interior 3-orbits, one interior 6-orbit. No
-#     positive degree-10 rule of this structure was found by multistart search; the
-#     degree-9 (= 2k - 1) equations leave a two-parameter family, fixed here by placing the
-#     edge pairs at t = 0.19 and t = 0.40: two-digit values of the member with the largest
-#     stable time step (smallest spectral radius of M^-1 K on an equilateral element, the
-#     quantity of Eq. spectral); the interior positions and all weights then follow from
-#     the twelve degree-9 equations.
+#   KMV5tri: vertices, two edge pairs, three interior 3-orbits and one interior 6-orbit
+#     (3 + 12 + 15 = 30 nodes), every position free; the moment equations up to degree
+#     10 = k + k' - 2 (k' = 7, the degree of b*P4) are 14 S3-invariant conditions on 14
+#     unknowns. Multistart Gauss-Newton finds one positive, unisolvent solution (the
+#     same one from every start that converges); the starts below lie near it.
 _KMV4_KINDS = ["v", "m", "e", "3", "3"]
 _KMV4_START = [0.21, 0.42, 0.13]
 _KMV4_DEGREE = 7
-_KMV5_KINDS = ["v", ("e", 0.19), ("e", 0.40), "3", "3", "3", "6"]
-_KMV5_START = [0.08, 0.47, 0.38, 0.61, 0.28]
-_KMV5_DEGREE = 9
+_KMV5_KINDS = ["v", "e", "e", "3", "3", "3", "6"]
+_KMV5_START = [0.36, 0.13, 0.058, 0.46, 0.26, 0.22, 0.70]
+_KMV5_DEGREE = 10
 
 
 def _solved_tri_nodes(k):

@@ -421,11 +421,10 @@ bool build(int dim, int k, Element& el, std::string& err) {
       // vertices, edge midpoints, one edge pair, two interior (a,a,1-2a) orbits; exact to 7
       if (!solve_orbits("vme33", {}, {0.212L, 0.425L, 0.131L}, 7, gens, err)) return false;
     } else if (k == 5) {
-      // vertices, edge pairs held at t = 0.19 and 0.40 (the member of the degree-9 family
-      // with the largest stable time step, to two digits), three interior (a,a,1-2a) orbits
-      // and one (a,b,1-a-b) orbit; interior positions and weights from the degree-9
-      // (= 2k-1) moment equations (no positive degree-10 rule of this structure is known)
-      if (!solve_orbits("vEE3336", {0.19L, 0.40L}, {0.077L, 0.474L, 0.381L, 0.613L, 0.279L}, 9,
+      // vertices, two edge pairs, three interior (a,a,1-2a) orbits and one (a,b,1-a-b)
+      // orbit, all positions free; exact to degree 10 = k + k' - 2 (k' = 7 for b*P4): 14
+      // symmetric moment conditions on 14 unknowns, one positive unisolvent solution
+      if (!solve_orbits("vee3336", {}, {0.36L, 0.13L, 0.058L, 0.46L, 0.26L, 0.22L, 0.70L}, 10,
                         gens, err))
         return false;
     } else {

@@ -65,7 +65,7 @@ def _patch_degree(kind, k):
     grad phi_i . grad u and phi_i Lap u must be integrated exactly, i.e.
     k' + m - 2 <= D with k' the top degree of the space and D the rule's exactness."""
     kp = {("tri", 2): 3, ("tri", 3): 4, ("tri", 4): 5, ("tri", 5): 7, ("tet", 2): 4, ("tet", 3): 5}
-    D = {("tri", 2): 3, ("tri", 3): 5, ("tri", 4): 7, ("tri", 5): 9, ("tet", 2): 3, ("tet", 3): 5}
+    D = {("tri", 2): 3, ("tri", 3): 5, ("tri", 4): 7, ("tri", 5): 10, ("tet", 2): 3, ("tet", 3): 5}
     return D[(kind, k)] - kp[(kind, k)] + 2
 
 
