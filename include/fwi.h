@@ -20,9 +20,11 @@
  *   - Bulk signal arrays (wavelets, records, residuals, gradients) may be host or device
  *     pointers: the library asks the CUDA runtime which one it is. Host arrays are staged
  *     through library-owned device buffers with copies on the caller's stream.
- *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
- *     asynchronous with respect to the host only when every bulk pointer is a device
- *     pointer; otherwise they return after the copies back to host memory complete.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). The work of a call
+ *     is queued on that stream, and every solve (forward, adjoint, gradient) then reads
+ *     the batch's device status flag back and synchronises the stream before it returns,
+ *     so that a non-finite wavefield or a kernel that gave up is reported by the call
+ *     that caused it. Calls therefore return only after their work has completed.
  *   - All device state (mesh, wavefields, checkpoints) is owned by the library and freed
  *     by fwi_batch_free / fwi_mesh_free. Handles are not thread-safe; distinct handles
  *     may be used from distinct threads.
@@ -131,6 +133,15 @@ int fwi_element(const fwi_mesh* m, int* n, double* xhat, double* w, double* dhat
 int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, double* dhat,
                           int* exact_degree);
 
+/* Point location (host only; works on host-only meshes): for each of npts points pts[p][dim]
+ * the containing element in the library's element order and the point's reference
+ * coordinates xhat[p][dim] (Section 4.3: sources and receivers are evaluated through the
+ * basis of the element that holds them). Ties (a point on a shared edge or vertex) go to
+ * the lowest element of the caller's cell order whose barycentric coordinates are all >=
+ * -1e-12. A point in no element gives FWI_EINVAL. elem_out or xhat_out may be NULL. */
+int fwi_locate(const fwi_mesh* m, const double* pts, int npts, int32_t* elem_out,
+               double* xhat_out);
+
 /* Sets the P-wavespeed at the DoFs (Section 4.6: c varies inside an element), c[N] host
  * doubles in the order of fwi_dof_coords, all > 0. Recomputes c^2, the lumped damping
  * coefficients and, if params.dt <= 0, the time step. */
@@ -165,21 +176,30 @@ int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes);
  * adjoint needs. */
 int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
 
-/* Allocation-free variant of fwi_forward_shot (the paper has no counterpart: this is a
- * deployment aid). For callers that cannot call cudaMalloc while they run -- code inside a
- * CUDA stream capture, where allocating is not allowed, or a service with a fixed device
- * memory budget reserved at start-up. It runs the same forward solve on the batch's
- * existing state and writes the records, but calls no cudaMalloc, cudaFree or allocating
- * library routine: the accumulator of the DoFs finished by the node kernel lives in a
- * file-scope static __device__ array of 4 Mi floats (16 MiB) that every GPU loading the
- * library holds until the process exits. It needs (halo DoFs, or shared DoFs for the plain
- * layout) x shots <= 4 Mi floats and returns FWI_EINVAL beyond that. The array's device
- * address is looked up (cudaGetSymbolAddress) on the first call on each device, so make
- * that first call before any stream capture. Every call shares the array and clears it
- * first; calls that overlap on the GPU (other streams, other threads, other batches) race
- * on it and must be serialised by the caller. wavelet[S][Nt] and rec_out[S][Nt+1][R] must
- * be device pointers (FWI_EINVAL otherwise); no checkpoints are stored, so this call does
- * not prepare an adjoint. */
+/* Allocation-free variant of fwi_forward_shot. The paper has no counterpart: this entry
+ * point exists for deployment. It serves callers that cannot allocate device memory while
+ * they run, for example a shot service that reserves its whole device memory budget at
+ * start-up (an allocation in mid-run could fail, fragment that budget or stall other
+ * streams), or a host process whose device memory is handed out by an external allocator
+ * that the library cannot call.
+ *
+ * It runs the same forward solve as fwi_forward_shot on the batch's existing state and
+ * writes the records. It calls no cudaMalloc, cudaFree or allocating library routine. The
+ * only scratch it needs, the accumulator of the DoFs that the node kernel finishes, is a
+ * file-scope static __device__ array of 4 Mi floats (16 MiB). Every GPU that loads the
+ * library holds that array until the process exits.
+ *   - Limit: (halo DoFs, or shared DoFs for the plain layout) x shots <= 4 Mi floats;
+ *     beyond it the call returns FWI_EINVAL before launching anything.
+ *   - Set-up: the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current. Make that first call before any
+ *     stream capture on the device.
+ *   - Sharing: every call uses the same array and clears it first. Calls that overlap on
+ *     the GPU (other streams, threads or batches) race on it; the caller must serialise
+ *     them.
+ *   - wavelet[S][Nt] and rec_out[S][Nt+1][R] must be device pointers (FWI_EINVAL
+ *     otherwise). No checkpoints are stored, so this call does not prepare an adjoint.
+ *   - Like every solve here, it reads the status flag back and synchronises the stream
+ *     before it returns. */
 int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
 
 /* Discrete adjoint solve (Section 3.4, the transposed recurrence run backwards) driven by

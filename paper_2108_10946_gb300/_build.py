@@ -9,8 +9,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfwi_gb300.so")
-UNITS = ["kmv_tab.cpp", "api.cu", "kernels.cu", "inst_2_2.cu", "inst_2_3.cu", "inst_2_4.cu",
-         "inst_2_5.cu", "inst_3_2.cu", "inst_3_3.cu"]
+# (source, object name, extra flags): the element kernels are one source compiled once per
+# KMV element (triangles k = 2..5, tetrahedra k = 2, 3)
+UNITS = [("kmv_tab.cpp", "kmv_tab", []), ("api.cu", "api", []), ("kernels.cu", "kernels", [])] + [
+    ("inst.cu", f"inst_{d}_{k}", [f"-DKMV_DIM={d}", f"-DKMV_K={k}"])
+    for d, k in ((2, 2), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3))]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"]
 
@@ -37,12 +40,13 @@ def build(force=False, verbose=False):
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_unit(u):
-        obj = os.path.join(OUT, u + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, u), "-o", obj]
+    def compile_unit(unit):
+        src, name, extra = unit
+        obj = os.path.join(OUT, name + ".o")
+        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", os.path.join(SRC, src), "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {u}:\n{p.stdout}\n{p.stderr}")
+            raise RuntimeError(f"nvcc failed for {name}:\n{p.stdout}\n{p.stderr}")
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:

@@ -11,7 +11,6 @@ c changes the operator and not the time grid.
 
 All numerical work runs in the CUDA library; this module passes pointers.
 """
-import numpy as np
 import torch
 
 from . import lib
@@ -42,12 +41,6 @@ class FWIMisfit(torch.autograd.Function):
 def misfit(c, mesh, batch, wavelet, observed):
     """J(c) with autograd support (see FWIMisfit)."""
     return FWIMisfit.apply(c, mesh, batch, wavelet, observed)
-
-
-def mesh_independent_gradient(dJdc, mesh_mass):
-    """G = M^{-1} dJ/dc (Eq. gradient3) for a caller holding the lumped mass; the library's
-    fwi_gradient returns it directly."""
-    return np.asarray(dJdc) / np.asarray(mesh_mass)
 
 
 __all__ = ["FWIMisfit", "misfit", "lib"]

@@ -46,7 +46,12 @@ int dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return 0;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) return fail(FWI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();  // an allocation failure is not sticky: clear it for later checks
+    return fail(FWI_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                " bytes: " + cudaGetErrorString(e));
+  }
   return 0;
 }
 
@@ -920,6 +925,22 @@ int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, doubl
   return 0;
 }
 
+int fwi_locate(const fwi_mesh* m, const double* pts, int npts, int32_t* elem_out,
+               double* xhat_out) {
+  if (!m || (npts > 0 && !pts) || npts < 0) return fail(FWI_EINVAL, "fwi_locate: bad argument");
+  std::vector<int> ue;
+  std::vector<double> xh;
+  if (int rc = locate(m, pts, npts, ue, xh)) return rc;
+  std::vector<int> new_of_user(m->E);
+  for (int e = 0; e < m->E; ++e) new_of_user[m->order[e]] = e;
+  for (int p = 0; p < npts; ++p) {
+    if (elem_out) elem_out[p] = new_of_user[ue[p]];
+    if (xhat_out)
+      for (int c = 0; c < m->dim; ++c) xhat_out[(size_t)p * m->dim + c] = xh[(size_t)p * m->dim + c];
+  }
+  return 0;
+}
+
 int fwi_set_velocity(fwi_mesh* m, const double* c) {
   if (!m || !c) return fail(FWI_EINVAL, "null argument");
   if (int rc = check_device(m)) return rc;
@@ -1441,14 +1462,16 @@ int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out,
   if (int rc = noalloc_scratch(&scratch)) return rc;
   // the accumulator must start at zero (a failed earlier call may have left values)
   if (need) CUDA_TRY(cudaMemsetAsync(scratch, 0, need * sizeof(float), st));
-  const bool prof = b->prof;
-  b->prof = false;  // event timing would create events
   const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
-  if (int rc = zero_state(b, b->u, b->v, b->P, b->Y, st)) {
-    b->prof = prof;
-    return rc;
-  }
+  if (int rc = zero_state(b, b->u, b->v, b->P, b->Y, st)) return rc;
   if (rn) CUDA_TRY(cudaMemsetAsync(rec_out, 0, rn * sizeof(float), st));
+  // per-kernel event timing would create events: off for this call, restored on every exit
+  struct ProfOff {
+    fwi_batch* b;
+    bool was;
+    ~ProfOff() { b->prof = was; }
+  } prof_off{b, b->prof};
+  b->prof = false;
   forward_steps(b, 0, b->nt, wavelet, rec_out, false, st, scratch);
   if (b->R) {
     StepArgs a = base_args(b);
@@ -1458,7 +1481,6 @@ int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out,
     m->ks->launch_record(a, b->d_rec_elem, b->d_rec_phi, st);
     g_launches += 1;
   }
-  b->prof = prof;
   return check_status(b, st);
 }
 

@@ -1,12 +1,24 @@
-// Kernels for KMV3tri: dim 2, 12 nodes, 9 of them shared (vertex/edge/face).
+// Kernels of one KMV element, instantiated once per (dimension, degree): the build compiles
+// this file with -DKMV_DIM=d -DKMV_K=k for KMV2..5tri and KMV2..3tet. Nodes per element:
+// triangles 7, 12, 18, 30 (6, 9, 12, 15 of them on vertices and edges); tetrahedra 15, 32
+// (14, 28 on vertices, edges and faces).
 #include <algorithm>
 #include <vector>
 
 #include "fwi_internal.h"
 
+#if !defined(KMV_DIM) || !defined(KMV_K)
+#error "compile with -DKMV_DIM=<2|3> -DKMV_K=<degree>"
+#endif
+
 namespace fwi {
 namespace {
-constexpr int D = 2, NN = 12, NS = 9;
+constexpr int D = KMV_DIM;
+constexpr int NN = D == 2 ? (KMV_K == 2 ? 7 : KMV_K == 3 ? 12 : KMV_K == 4 ? 18 : 30)
+                          : (KMV_K == 2 ? 15 : 32);
+constexpr int NS = D == 2 ? 3 * KMV_K : (KMV_K == 2 ? 14 : 28);
+static_assert((D == 2 && KMV_K >= 2 && KMV_K <= 5) || (D == 3 && KMV_K >= 2 && KMV_K <= 3),
+              "KMV elements: triangles k = 2..5, tetrahedra k = 2, 3");
 __constant__ float c_dhat[D * NN * NN];
 __constant__ float c_w[NN];
 }  // namespace
@@ -14,12 +26,16 @@ __constant__ float c_w[NN];
 
 #include "step_kernel.cuh"
 #include "chunk_kernel.cuh"
+#if KMV_DIM == 2
 #include "chunk_tc.cuh"
+#endif
 
 namespace fwi {
 namespace {
+#if KMV_DIM == 2
 // Dhat as the B operands of the tensor-core kernel (hi and lo, canonical layout)
 __device__ __align__(16) float g_bimg[TcShape<D, NN>::BIMG];
+#endif
 
 __global__ void __launch_bounds__(128) k_step(const StepArgs a) { step_body<D, NN, NS>(a); }
 
@@ -51,6 +67,7 @@ int launch_chunk_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   return 0;
 }
 
+#if KMV_DIM == 2
 template <int MODE, bool LAYER>
 __global__ void __launch_bounds__(128) k_chunk_tc(const StepArgs a, int nrun) {
   extern __shared__ __align__(128) float smem_tc[];
@@ -87,10 +104,13 @@ int launch_chunk_tc_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   return 0;
 }
 
+#endif
+
 // chunks [0, nch0) hold no damping-layer element, chunks [nch0, nch) do
 int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
   const int mode = a.mode == 0 ? 0 : (a.ring_u != nullptr ? 2 : 1);
   int rc = 0;
+#if KMV_DIM == 2
   if (a.tc && mode != 0) {  // the adjoint steps only
     switch (mode) {
       case 1:
@@ -103,6 +123,7 @@ int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
     }
     return rc;
   }
+#endif
   switch (mode) {
     case 0:
       rc = launch_chunk_t<0, false>(a, 0, a.nch0, st);
@@ -122,11 +143,13 @@ int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
 int upload(const float* dhat, const float* w) {
   cudaError_t e = cudaMemcpyToSymbol(c_dhat, dhat, sizeof(float) * D * NN * NN);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w, w, sizeof(float) * NN);
+#if KMV_DIM == 2
   if (e == cudaSuccess) {
     std::vector<float> img(TcShape<D, NN>::BIMG);
     tc_build_bimg<D, NN>(dhat, img.data());
     e = cudaMemcpyToSymbol(g_bimg, img.data(), sizeof(float) * img.size());
   }
+#endif
   return (int)e;
 }
 
@@ -143,5 +166,10 @@ void launch_record(const StepArgs& a, const int* rec_elem, const float* rec_phi,
 }
 }  // namespace
 
-extern const KernelSet kernels_2_3 = {D, 3, NN, NS, NN - NS, upload, launch_step, launch_chunk, launch_record};
+#define KMV_CAT2(a, b, c, d) a##b##c##d
+#define KMV_CAT(a, b, c, d) KMV_CAT2(a, b, c, d)
+extern const KernelSet KMV_CAT(kernels_, KMV_DIM, _, KMV_K) = {D,           KMV_K,       NN,
+                                                              NS,          NN - NS,     upload,
+                                                              launch_step, launch_chunk,
+                                                              launch_record};
 }  // namespace fwi

@@ -12,7 +12,7 @@ import numpy as np
 
 from . import _build
 
-FWI_EINVAL, FWI_ENOMEM, FWI_ERANGE, FWI_ECUDA = -22, -12, -34, -5
+FWI_EINVAL, FWI_ENOMEM, FWI_ERANGE, FWI_ECUDA, FWI_ETIMEDOUT = -22, -12, -34, -5, -110
 
 
 class FwiError(RuntimeError):
@@ -57,6 +57,7 @@ def load():
         "fwi_dof_coords": (ctypes.c_int, [_P, _P]),
         "fwi_element": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P, _P]),
         "fwi_set_velocity": (ctypes.c_int, [_P, _P]),
+        "fwi_locate": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
         "fwi_reference_element": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                  _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
         "fwi_get_dt": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -200,6 +201,15 @@ class Mesh:
         sig = np.zeros((self.N, self.dim))
         _check(_lib.fwi_mesh_host_arrays(self._h, _ptr(conn), _ptr(M), _ptr(Mb), _ptr(sig)))
         return conn, M, Mb, sig
+
+    def locate(self, pts):
+        """(element index in the library's order [npts], reference coordinates [npts][dim])
+        of each point; raises FwiError(FWI_EINVAL) for a point outside the mesh."""
+        pts = np.ascontiguousarray(np.atleast_2d(pts), dtype=np.float64)
+        el = np.zeros(pts.shape[0], dtype=np.int32)
+        xh = np.zeros((pts.shape[0], self.dim))
+        _check(_lib.fwi_locate(self._h, _ptr(pts), pts.shape[0], _ptr(el), _ptr(xh)))
+        return el, xh
 
     def set_velocity(self, c):
         c = np.ascontiguousarray(c, dtype=np.float64)

@@ -67,3 +67,34 @@ class OracleCase:
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ---- oracle shots in a process pool (spawn start: safe next to a CUDA context) ------------
+
+def _oracle_shot(args):
+    spec, src, recs, wavelet, res_scale = args
+    from synth import models
+    model = models.marine2d(spec.get("model_seed", 0))
+    orc = OracleCase(spec["V"], spec["cells"], spec["k"], model, spec["dt"], spec["nt"],
+                     layer=spec["layer"], absorbing=spec["absorbing"], water=spec["water"])
+    need_grad = res_scale is not None
+    rec, U = orc.forward(src, recs, wavelet, store=need_grad)
+    g = None
+    if need_grad:
+        H = assemble.point_matrix(orc.mesh, recs)
+        _, g = orc.ops.adjoint(H, res_scale * rec.astype(np.float32).astype(np.float64), U_hist=U)
+    return rec, g
+
+
+def oracle_shots(spec, srcs, recs, wavelets, res_scale=None, workers=4):
+    """FP64 oracle records (and, if res_scale is given, the raw gradient sums g of Eq.
+    gradient3 for the residual res_scale * float32(records)) of every shot on the marine
+    model, one shot per worker of a spawn-started process pool. spec: V, cells, k, dt, nt,
+    layer (dict or None), absorbing, water."""
+    import multiprocessing as mp
+    jobs = [(spec, np.asarray(s, np.float64), np.asarray(recs, np.float64),
+             np.asarray(w, np.float64), res_scale) for s, w in zip(srcs, wavelets)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(workers, len(jobs))) as pool:
+        out = pool.map(_oracle_shot, jobs)
+    return [o[0] for o in out], [o[1] for o in out]

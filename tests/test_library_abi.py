@@ -74,3 +74,82 @@ def test_tensor_cores_refused_where_there_is_no_such_kernel(dim, layout):
     m = pkg.Mesh(V, C, 2, 10, dt=1e-3, host_only=True, layout=layout, tensor_cores=0)
     assert m.N > 0
     m.close()
+
+
+# ---- error paths of the boundary (host side, no GPU) -------------------------------------
+
+def _host_mesh(V, C, k=2, **kw):
+    import paper_2108_10946_gb300 as pkg
+    pkg.build()
+    return pkg.Mesh(V, C, k, 10, dt=1e-3, host_only=True, **kw)
+
+
+def test_inverted_cell_is_refused_with_einval():
+    """An element with det J <= 0 (its vertices listed clockwise) is an invalid mesh: the
+    library returns FWI_EINVAL and names the element."""
+    import paper_2108_10946_gb300.lib as L
+    from synth import meshes
+    V, C = meshes.structured_tri(4, 4)
+    C = C.copy()
+    C[5] = C[5][[0, 2, 1]]
+    with pytest.raises(L.FwiError, match="det J") as ei:
+        _host_mesh(V, C)
+    assert ei.value.code == L.FWI_EINVAL
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_point_outside_the_mesh_is_refused_with_einval(dim):
+    """Point location (Section 4.3) of a receiver outside the domain: FWI_EINVAL; points
+    inside (including a shared vertex) are found with reference coordinates that map back
+    to the point."""
+    import numpy as np
+    import paper_2108_10946_gb300.lib as L
+    from synth import meshes
+    if dim == 2:
+        V, C = meshes.structured_tri(6, 6)
+        inside = np.array([[0.31, 0.72], [0.5, 0.5], [0.0, 0.0]])
+        outside = np.array([[0.3, 0.2], [1.2, 0.5]])
+    else:
+        g = np.linspace(0.0, 1.0, 4)
+        V, C = meshes.kuhn_tets(g, g, g)
+        inside = np.array([[0.31, 0.72, 0.4], [1 / 3, 1 / 3, 1 / 3]])
+        outside = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, -0.01]])
+    m = _host_mesh(V, C)
+    el, xh = m.locate(inside)
+    conn = m.host_arrays()[0]
+    xyz = m.dof_coords()
+    nv = dim + 1  # the first dim+1 local nodes of every element are its vertices
+    for p in range(len(inside)):
+        X = xyz[conn[el[p], :nv]]
+        back = X[0] + (X[1:] - X[0]).T @ xh[p]
+        assert np.allclose(back, inside[p], atol=1e-12)
+    with pytest.raises(L.FwiError, match="outside the mesh") as ei:
+        m.locate(outside)
+    assert ei.value.code == L.FWI_EINVAL
+    m.close()
+
+
+def test_batch_bytes_counts_every_device_array():
+    """fwi_batch_bytes, the admission test of the shot server, against the sizes of the
+    arrays a batch allocates (host-only mesh, no GPU): wavefields, layer auxiliaries,
+    checkpoints, the recompute ring, accumulators and the signal copies."""
+    import numpy as np
+    from synth import meshes, signals
+    V, C = meshes.structured_tri(12, 10, 1.2, 1.0, -0.1, 0.0)
+    m = _host_mesh(V, C, k=3, box=[(0.0, 1.0), (-10.0, 0.9)], layer_faces=0b1011,
+                   layer_width=0.1, sigma_max=signals.sigma_max(2.0, 0.1), ckpt_stride=7)
+    S, R, nt = 4, 9, 10
+    N = m.N
+    conn = m.host_arrays()[0]
+    sig = m.host_arrays()[3]
+    # DoFs of damping-layer elements (an element is one when a vertex lies inside the
+    # layer; the first dim + 1 local nodes are the vertices) carry the layer auxiliaries
+    layer_el = np.any(np.any(sig[conn[:, :3]] > 0, axis=2), axis=1)
+    Nl = len(np.unique(conn[layer_el]))
+    C_ = -(-nt // 7)
+    state = S * (2 * N + Nl * 2)
+    floats = (3 * N * S + 3 * Nl * 2 * S + 2 * Nl * S + 2 * N * S + Nl * 2 * S + Nl * S
+              + state * C_ + N * S * 7 + N + 2 * S * (nt + 1) * R + S * nt)
+    expect = floats * 4 + 2 * N * 8 + m.E * 4
+    assert m.batch_bytes(S, R) == expect
+    m.close()
