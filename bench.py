@@ -29,7 +29,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAK_HBM_FALLBACK = 6800.0
-SM_COUNT, FP32_LANES = 152, 128
 
 
 METRIC = "DoF-steps/s (forward + adjoint, FP32, <=1e-5 rel-L2 vs FP64 oracle)"
@@ -123,34 +122,74 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_rate(wl, nsteps=200, budget_s=15.0):
-    """FP64 oracle DoF-steps/s (forward + adjoint) on a bounded sample: a 2 km x 1.5 km window
-    of the same model and element degree, a handful of steps. Single-threaded sparse algebra."""
+# ---- the FP64 oracle on the host cores (cpu_baseline, parity sample, reference arm) ----------
+# One shot per worker of a spawn-started process pool (the paper's ensemble runs one shot per
+# core). Each worker builds the oracle for the small marine window of the workload once.
+_ORC = {}
+
+
+def _orc_init(k):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from parity_util import OracleCase
-    from synth import signals
-    small = make_workload(k=wl["k"], small=True)
-    model = small["model"]
-    probe = OracleCase(small["V"], small["cells"], wl["k"], model, 1.0, 1, layer=small["layer"],
-                       absorbing=True)
+    small = make_workload(k=k, small=True)
+    lay = small["layer"]
+    probe = OracleCase(small["V"], small["cells"], k, small["model"], 1.0, 1, layer=lay,
+                       absorbing=True, water=1.51)
     dt = 0.9 * probe.ops.cfl_dt()
-    orc = OracleCase(small["V"], small["cells"], wl["k"], model, dt, nsteps, layer=small["layer"],
-                     absorbing=True)
-    w = signals.ricker_samples(wl["f"], dt, nsteps).astype(np.float64)
+    orc = OracleCase(small["V"], small["cells"], k, small["model"], dt, 1, layer=lay,
+                     absorbing=True, water=1.51)
+    _ORC.update(k=k, small=small, dt=dt, orc=orc)
+
+
+def _orc_shot(job):
+    """Forward (history stored) and adjoint with the gradient integrand for one shot;
+    returns (records, raw gradient sum or None, DoF-steps, seconds)."""
+    from oracle import assemble
+    src, nt, wav, res_scale, keep = job
+    orc = _ORC["orc"]
+    orc.nt = nt
     t0 = time.perf_counter()
-    done = 0
-    while True:
-        rec, U = orc.forward(small["srcs"][0], small["recs"], w, store=True)
-        from oracle import assemble
-        H = assemble.point_matrix(orc.mesh, small["recs"])
-        orc.ops.adjoint(H, rec, U_hist=U)
-        done += 1
-        if time.perf_counter() - t0 > budget_s or done >= 20:
-            break
+    rec, U = orc.forward(src, _ORC["small"]["recs"], wav, store=True)
+    H = assemble.point_matrix(orc.mesh, _ORC["small"]["recs"])
+    _, g = orc.ops.adjoint(H, res_scale * rec.astype(np.float32).astype(np.float64), U_hist=U)
     el = time.perf_counter() - t0
-    dofsteps = done * orc.mesh.N * nsteps * 2
-    return dict(value=dofsteps / el, cores=1, N=orc.mesh.N, E=orc.mesh.E, nsteps=nsteps, reps=done,
-                seconds=el)
+    return (rec if keep else None), (g if keep else None), orc.mesh.N * nt * 2, el
+
+
+def oracle_pool(k, workers):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers, initializer=_orc_init, initargs=(k,))
+
+
+def oracle_window_info(k):
+    _orc_init(k)
+    return dict(dt=_ORC["dt"], N=_ORC["orc"].mesh.N, E=_ORC["small"]["cells"].shape[0],
+                small=_ORC["small"], orc=_ORC["orc"])
+
+
+def parity_shots(small, n):
+    """n shot positions at 50 m depth across the small window."""
+    return np.stack([np.linspace(6.3, 7.7, n), np.full(n, 0.05)], 1)
+
+
+def oracle_rate(pool, k, dt, workers, nsteps):
+    """DoF-steps/s of the FP64 oracle (forward + adjoint with the gradient integrand) over
+    `workers` shots, one per worker, nsteps time steps each; wall-clock of the pool."""
+    from synth import signals
+    srcs = parity_shots(None, workers)
+    wav = signals.ricker_samples(5.0, dt, nsteps).astype(np.float64)
+    jobs = [(srcs[i], nsteps, wav, 0.03, False) for i in range(workers)]
+    t0 = time.perf_counter()
+    out = pool.map(_orc_shot, jobs)
+    wall = time.perf_counter() - t0
+    return dict(value=sum(o[2] for o in out) / wall, seconds=wall, nsteps=nsteps, shots=workers)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0, interarrivals=(0.008, 0.004, 0.002)):
@@ -219,34 +258,181 @@ def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0, interarrivals=(0.008, 0
 
 
 def run_reference(args):
+    """The oracle arm: the FP64 oracle on the host cores, one shot per core, each step a
+    bounded sample (ref_steps time steps of forward + adjoint per shot) of the workload's
+    small marine window at the same element degree."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl_k = args.k
-    wl = dict(k=wl_k, f=5.0)
-    vals = []
-    for _ in range(args.warmup):
-        oracle_rate(wl, budget_s=5.0)
-    t0 = time.perf_counter()
-    last = None
-    for _ in range(args.steps):
-        last = oracle_rate(wl, budget_s=10.0)
-        vals.append(last["value"])
-    el = time.perf_counter() - t0
+    k = args.k
+    cores = host_cores()
+    info = oracle_window_info(k)
+    pool = oracle_pool(k, cores)
+    try:
+        for _ in range(args.warmup):
+            oracle_rate(pool, k, info["dt"], cores, args.ref_steps)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(oracle_rate(pool, k, info["dt"], cores, args.ref_steps)["value"])
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
     v = float(np.mean(vals))
-    sample = (f"FP64 oracle, KMV{wl_k}tri window of the marine model (2 km x 1.5 km, "
-              f"{last['E']} elements, N={last['N']}), {last['nsteps']} forward + adjoint steps per rep")
+    sample = (f"FP64 oracle, KMV{k}tri on the 2 km x 1.5 km marine window of the workload "
+              f"({info['E']} elements, N={info['N']}), {cores} shots (one per host core), "
+              f"{args.ref_steps} forward + adjoint steps each per bench step")
     line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * el / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(wl_k),
-                       "sample": "the FP64 oracle on one host core, timed on a bounded window of "
+            "config": {"workload": workload_name(k),
+                       "sample": "the FP64 oracle on the host cores, timed on a bounded window of "
                                  "the workload (see cpu_baseline.sample)"},
-            "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def parity_sample(pkg, pool, info, k, S, T_par):
+    """The GPU library against the FP64 oracle on the workload's small marine window (same
+    mesher, model, water, layer and absorbing boundary; S shots, T_par seconds): records
+    rel-L2 (worst shot) and gradient rel-L2, as the tests measure them. The oracle shots run
+    in the pool; the GPU runs the same shots as one batch."""
+    import torch
+    from synth import signals
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_util import match_dofs, rel_l2
+    dt, small, orc = info["dt"], info["small"], info["orc"]
+    nt = int(round(T_par / dt))
+    srcs = parity_shots(small, S)
+    wav = signals.ricker_samples(5.0, dt, nt).astype(np.float32)
+    out = pool.map(_orc_shot, [(srcs[i], nt, wav.astype(np.float64), 0.03, True) for i in range(S)])
+    lay = small["layer"]
+    mesh = pkg.Mesh(small["V"], small["cells"], k, nt, dt=dt, box=lay["box"],
+                    layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"],
+                    absorbing=True, ckpt_stride=50, water_speed=1.51)
+    xg = mesh.dof_coords()
+    mesh.set_velocity(small["model"](xg))
+    b = pkg.Batch(mesh, srcs, small["recs"])
+    rec = torch.zeros((S, nt + 1, len(small["recs"])), device="cuda")
+    b.forward(torch.from_numpy(np.stack([wav] * S)).cuda(), rec)
+    rec = rec.cpu().numpy()
+    rec_err = max(rel_l2(rec[s], out[s][0]) for s in range(S))
+    res = np.stack([0.03 * o[0].astype(np.float32) for o in out]).astype(np.float32)
+    b.adjoint(torch.from_numpy(res).cuda())
+    G = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+    b.gradient(G)
+    perm = match_dofs(orc.mesh.coords, xg, 1.0)
+    Go = orc.ops.gradient(np.sum([o[1] for o in out], axis=0), orc.mask)
+    g_err = rel_l2(G.cpu().numpy()[perm], Go)
+    b.close()
+    mesh.close()
+    return {"records_rel_l2_max": rec_err, "gradient_rel_l2": g_err, "shots": S, "steps": nt,
+            "window": f"2 km x 1.5 km marine window, KMV{k}, N={info['N']}, {T_par} s, water, "
+                      f"layer, absorbing boundary, residual 0.03 d"}
+
+
+NODES = {2: (7, 6), 3: (12, 9), 4: (18, 12), 5: (30, 15)}  # KMVktri: nodes, shared nodes
+
+
+def step_roofline(prof, k, E, N, S, fp32_tflops, sm_count, peaks, src):
+    """Roofline entries of the forward time step (element kernels + shared-DoF kernel) and of
+    the adjoint step with the gradient integrand, from per-step CUDA-event times.
+    Algorithmic work per step (stated in DESIGN):
+      forward flops = E S 4 d n^2 (two n x n contractions per direction per element and shot)
+      adjoint flops = E S 6 d n^2 (plus the contraction of the forward field)
+      forward bytes = N (16 S + 8) + E (4 n_s + 12): u, v read and written per shot, c^2 and
+                      M^-1 per DoF, shared-node connectivity and Ghat per element
+      adjoint bytes = forward bytes + 4 N S (forward field) + 8 N (gradient segment)"""
+    nn, ns = NODES[k]
+    d = 2
+    fs, as_ = max(prof["fwd_steps"], 1), max(prof["adj_steps"], 1)
+    fwd_ms = (prof["fwd_elem_ms"] + prof["fwd_node_ms"]) / fs
+    adj_ms = (prof["adj_elem_ms"] + prof["adj_node_ms"]) / as_
+    hbm = peaks["hbm_gbs"]
+
+    def entry(flops, nbytes, ms, label):
+        tf = flops / (ms * 1e-3) / 1e12
+        gb = nbytes / (ms * 1e-3) / 1e9
+        alu_src = f"measured FP32 FMA probe (fwi_fp32_peak), {sm_count} SMs"
+        if tf / fp32_tflops >= gb / hbm:
+            e = {"bound": "alu", "achieved": tf, "peak": fp32_tflops, "unit": "TFLOP/s",
+                 "frac": tf / fp32_tflops, "peak_source": alu_src, "hbm_achieved_gbs": gb,
+                 "hbm_frac": gb / hbm}
+        else:
+            e = {"bound": "hbm", "achieved": gb, "peak": hbm, "unit": "GB/s", "frac": gb / hbm,
+                 "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs", "alu_achieved_tflops": tf,
+                 "alu_frac": tf / fp32_tflops}
+        e.update({"traffic": None, "kernel": f"{label}, {ms * 1e3:.1f} us/step",
+                  "flops_per_step": flops, "bytes_per_step": nbytes})
+        return e
+
+    fwd_bytes = N * (16 * S + 8) + E * (4 * ns + 12)
+    roof = entry(E * S * 4 * d * nn * nn, fwd_bytes, fwd_ms,
+                 "forward time step (element kernels + shared-DoF kernel)")
+    roof["element_kernel_us"] = prof["fwd_elem_ms"] / fs * 1e3
+    roof["node_kernel_us"] = prof["fwd_node_ms"] / fs * 1e3
+    roof["adjoint"] = entry(E * S * 6 * d * nn * nn, fwd_bytes + 4 * N * S + 8 * N, adj_ms,
+                            "adjoint step with the gradient integrand")
+    roof["adjoint"]["element_kernel_us"] = prof["adj_elem_ms"] / as_ * 1e3
+    roof["adjoint"]["node_kernel_us"] = prof["adj_node_ms"] / as_ * 1e3
+    return roof
+
+
+def degree_line(pkg, k, args, S, fp32_tflops, sm_count, peaks, src):
+    """The same step (forward, adjoint, gradient) on the marine workload at another element
+    degree, over a shorter window: DoF-steps/s and the roofline entries."""
+    import torch
+    from synth import signals
+    wl = make_workload(k=k)
+    lay = wl["layer"]
+    kw = dict(box=lay["box"], layer_faces=lay["faces"], layer_width=lay["width"],
+              sigma_max=lay["smax"], absorbing=True, ckpt_stride=args.ckpt, water_speed=1.51)
+    m0 = pkg.Mesh(wl["V"], wl["cells"], k, 1, dt=0.0, cfl_factor=0.9, **kw)
+    c = wl["model"](m0.dof_coords())
+    m0.set_velocity(c)
+    dt = m0.dt
+    m0.close()
+    nt = args.extra_window
+    mesh = pkg.Mesh(wl["V"], wl["cells"], k, nt, dt=dt, **kw)
+    mesh.set_velocity(c)
+    b = pkg.Batch(mesh, wl["srcs"][:S], wl["recs"])
+    R = len(wl["recs"])
+    wav = torch.from_numpy(np.stack([signals.ricker_samples(5.0, dt, nt)] * S)).float().cuda()
+    rec = torch.zeros((S, nt + 1, R), device="cuda")
+    obs = torch.zeros_like(rec)
+    G = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+    b.forward(wav, obs)
+    obs *= 0.97
+
+    def step():
+        b.forward(wav, rec)
+        b.adjoint_misfit(obs)
+        b.gradient(G)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    b.profile(True)
+    step()
+    prof = b.profile_read()
+    b.profile(False)
+    out = {"k": k, "workload": workload_name(k), "elements": mesh.E, "dofs": mesh.N, "dt": dt,
+           "window_steps": nt, "shots_per_step": S, "ms_per_step": ms,
+           "value": S * mesh.N * nt * 2 / (ms * 1e-3), "unit": "DoF-steps/s",
+           "roofline": step_roofline(prof, k, mesh.E, mesh.N, S, fp32_tflops, sm_count, peaks, src)}
+    b.close()
+    mesh.close()
+    return out
 
 
 def run_ours(args):
@@ -263,6 +449,12 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pkg.build()
+    pool = info = None
+    cores = host_cores()
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's worker pool starts now (spawn) and builds its window while the GPU runs
+        pool = oracle_pool(args.k, cores)
+    fp32_tflops, sm_count = pkg.lib.fp32_peak()
     wl = make_workload(k=args.k, C=args.C)
     lay = wl["layer"]
     t_setup = time.perf_counter()
@@ -347,33 +539,21 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_val = S * N * nt * 2 * world / e2e_s
 
-    # per-kernel timing of the forward step (events on the library's stream)
+    # per-kernel timing of the forward and adjoint steps (events on the library's stream)
     batch.profile(True)
     batch.forward(wav_d, rec_d)
+    batch.adjoint_misfit(obs_d)
+    batch.gradient(G_d)
     prof = batch.profile_read()
     batch.profile(False)
-    fwd_ms = (prof["fwd_elem_ms"] + prof["fwd_node_ms"]) / max(prof["fwd_steps"], 1)
-    nn = {2: 7, 3: 12, 4: 18, 5: 30}[wl["k"]]
-    ns = {2: 6, 3: 9, 4: 12, 5: 15}[wl["k"]]
-    flops = E * 4 * 2 * nn * nn * S
-    bytes_alg = N * (16 * S + 8) + E * (4 * ns + 12)
     peaks, src = _peaks()
     clk_sum = clk.summary(local)
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    achieved_tf = flops / (fwd_ms / 1000.0) / 1e12
-    achieved_gb = bytes_alg / (fwd_ms / 1000.0) / 1e9
-    hbm_peak = peaks["hbm_gbs"]
-    if achieved_tf / alu_peak >= achieved_gb / hbm_peak:
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak, "traffic": None,
-                "hbm_frac": achieved_gb / hbm_peak, "hbm_achieved_gbs": achieved_gb,
-                "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved_gb, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gb / hbm_peak, "traffic": None, "alu_frac": achieved_tf / alu_peak,
-                "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"}
-    roof["kernel"] = f"forward time step (element + shared-DoF kernels), {fwd_ms*1000:.1f} us/step"
+    roof = step_roofline(prof, wl["k"], E, N, S, fp32_tflops, sm_count, peaks, src)
+
+    extra_k = []
+    if rank == 0 and args.extra_k:
+        for kx in [int(x) for x in args.extra_k.split(",") if x]:
+            extra_k.append(degree_line(pkg, kx, args, S, fp32_tflops, sm_count, peaks, src))
 
     plain = None
     if args.plain:
@@ -411,13 +591,20 @@ def run_ours(args):
     if rank == 0 and not args.no_serving:
         serving = serving_stream(pkg)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        ob = oracle_rate(dict(k=wl["k"], f=wl["f"]))
-        cpu = {"value": ob["value"], "unit": "DoF-steps/s", "cores": ob["cores"], "kind": "oracle",
-               "sample": (f"FP64 oracle, KMV{wl['k']}tri on a 2 km x 1.5 km window of the same "
-                          f"model ({ob['E']} elements, N={ob['N']}), {ob['nsteps']} forward + adjoint "
-                          f"steps x {ob['reps']}, {ob['seconds']:.1f} s")}
+    cpu = parity = None
+    if pool is not None:
+        try:
+            info = oracle_window_info(wl["k"])
+            parity = parity_sample(pkg, pool, info, wl["k"], S, {2: 1.0, 3: 0.8, 4: 0.5, 5: 0.3}[wl["k"]])
+            ob = oracle_rate(pool, wl["k"], info["dt"], cores, args.ref_steps)
+        finally:
+            pool.close()
+            pool.join()
+        cpu = {"value": ob["value"], "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 oracle, KMV{wl['k']}tri on the 2 km x 1.5 km marine window of the "
+                          f"workload ({info['E']} elements, N={info['N']}), {cores} shots in "
+                          f"parallel (one per host core), {ob['nsteps']} forward + adjoint steps each, "
+                          f"{ob['seconds']:.1f} s wall")}
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -436,6 +623,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(rec_h.numel() * 4 + N * 8)},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "parity_vs_oracle": parity,
+            "other_degrees": extra_k,
             "cpu_baseline": cpu,
             "plain_form": plain,
             "serving": serving,
@@ -463,11 +652,35 @@ def main():
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream latency run")
+    ap.add_argument("--extra-k", default="3,4",
+                    help="other element degrees measured on the same workload (comma list; '' for none)")
+    ap.add_argument("--extra-window", type=int, default=500)
+    ap.add_argument("--ref-steps", type=int, default=300,
+                    help="time steps per shot of the oracle's timed sample")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        spawn_ranks(args)
     else:
         run_ours(args)
+
+
+def _rank_main(rank, args, port):
+    os.environ.update({"RANK": str(rank), "LOCAL_RANK": str(rank), "WORLD_SIZE": str(args.gpus),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    run_ours(args)
+
+
+def spawn_ranks(args):
+    """bench.py --gpus N without a launcher: start one process per GPU (spawn), with the
+    rank variables a launcher would set; rank 0 prints the line."""
+    import socket
+    import torch.multiprocessing as tmp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    tmp.start_processes(_rank_main, args=(args, port), nprocs=args.gpus, start_method="spawn")
 
 
 if __name__ == "__main__":

@@ -142,6 +142,15 @@ int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, doubl
 int fwi_locate(const fwi_mesh* m, const double* pts, int npts, int32_t* elem_out,
                double* xhat_out);
 
+/* The FP32 copies of dhat[dim][n][n] and w[n] that the kernels use (host only). They are not
+ * the nearest FP32 values: each derivative row is rounded so that it still differentiates
+ * every polynomial of degree <= 2 at its node as exactly as FP32 allows, and the weights so
+ * that they still integrate 1 and the coordinates. Rounding every entry to nearest leaves
+ * the same error in every element; in a long record it shifts the discrete frequencies
+ * coherently and the phase error of the seismograms grows linearly with time. Either pointer
+ * may be NULL. */
+int fwi_reference_element_f32(int dim, int k, float* dhat, float* w);
+
 /* Sets the P-wavespeed at the DoFs (Section 4.6: c varies inside an element), c[N] host
  * doubles in the order of fwi_dof_coords, all > 0. Recomputes c^2, the lumped damping
  * coefficients and, if params.dt <= 0, the time step. */
@@ -238,6 +247,13 @@ int fwi_mesh_free(fwi_mesh* m);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated to len). */
 int fwi_last_error(char* buf, int len);
+
+/* Measurement aid (no counterpart in the paper): the FP32 FMA throughput of the current
+ * device in TFLOP/s, from a kernel of independent packed FP32x2 FMA chains on every SM (best
+ * of five timed launches, CUDA events), and its SM count. The element kernels, at 4 d n^2
+ * flops per element and shot, are bound by this rate; it is the denominator of their roofline
+ * fraction. Allocates and frees a 16 KiB buffer. */
+int fwi_fp32_peak(double* tflops, int* sm_count);
 
 /* Kernel launches the library issued on this thread since the last call (counter read and
  * reset). */

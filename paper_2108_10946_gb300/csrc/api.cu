@@ -115,12 +115,14 @@ struct fwi_mesh {
   const fwi::KernelSet* ks = nullptr;
   int64_t nverts = 0;
   int E = 0, E0 = 0, N = 0, Ns = 0, Nl = 0;
+  int Es = 0;         // element row stride of geo / lconn / inj (E rounded up to 32)
   int layout = 0;     // 0 chunked (shared-memory assembly), 1 plain (global atomics)
   bool use_tc = false;  // chunked 2D: element contractions on the tensor cores
   int P = 32;         // elements per chunk
   int N_own = 0;      // DoFs owned by one chunk: [0, N_own); halo DoFs [N_own, N)
   int nch0 = 0;       // chunks [0, nch0) have no damping-layer element
   int L_max = 0;      // largest local DoF table of a chunk (owned + halo)
+  int O_max = 0, H_max = 0;  // largest owned range and halo list of a chunk
   std::vector<int32_t> bub;                       // [E] first bubble DoF of every element
   std::vector<int32_t> ch_e0, ch_own_lo, ch_nsh;  // chunk element ranges, owned ranges
   std::vector<int32_t> ch_halo_ptr, halo_ids;     // per-chunk halo lists (global DoF ids)
@@ -220,7 +222,8 @@ int ensure_constants(fwi_mesh* m) {
   std::lock_guard<std::mutex> lk(mu);
   for (auto& d : done)
     if (d[0] == m->device && d[1] == m->dim && d[2] == m->k) return 0;
-  std::vector<float> dh(m->el.dhat.begin(), m->el.dhat.end()), w(m->el.w.begin(), m->el.w.end());
+  std::vector<float> dh, w;
+  kmvtab::fp32_tables(m->el, dh, w);
   int e = m->ks->upload_constants(dh.data(), w.data());
   if (e != 0) return fail(FWI_ECUDA, std::string("constant upload: ") + cudaGetErrorString((cudaError_t)e));
   done.push_back({m->device, m->dim, m->k});
@@ -358,7 +361,7 @@ int locate(const fwi_mesh* m, const double* pts, int npts, std::vector<int>& use
 void build_injection(const fwi_mesh* m, const fwi_batch* b, std::vector<int>& inj,
                      std::vector<int>& sptr, std::vector<int>& srec, std::vector<float>& sphi) {
   const int n = m->nn, S = b->S, nrec = b->R;
-  inj.assign(m->E, -1);
+  inj.assign((size_t)m->Es + 32, -1);  // padded to the element row stride
   std::vector<int> slot_elems;
   auto slot_of = [&](int e) {
     if (inj[e] < 0) {
@@ -487,6 +490,12 @@ int fwi_last_error(char* buf, int len) {
   return 0;
 }
 
+int fwi_fp32_peak(double* tflops, int* sm_count) {
+  int e = fwi::measure_fma_peak(tflops, sm_count);
+  if (e) return fail(FWI_ECUDA, std::string("FP32 peak probe: ") + cudaGetErrorString((cudaError_t)e));
+  return 0;
+}
+
 int64_t fwi_launch_count(void) {
   int64_t v = g_launches;
   g_launches = 0;
@@ -531,6 +540,7 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
   m->verts.assign(verts, verts + nverts * d);
   m->cells.assign(cells, cells + ncells * (d + 1));
   const int E = m->E = (int)ncells;
+  m->Es = (int)((ncells + 31) / 32 * 32);
   for (int64_t i = 0; i < ncells * (d + 1); ++i)
     if (cells[i] < 0 || cells[i] >= nverts) return fail(FWI_EINVAL, "cell vertex id out of range");
 
@@ -679,7 +689,7 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
     // per-chunk halo lists and local connectivity
     m->ch_halo_ptr.assign(nch + 1, 0);
     m->halo_ids.clear();
-    m->lconn.assign((size_t)m->ns * E, 0);
+    m->lconn.assign((size_t)m->ns * m->Es + 32, 0);
     m->L_max = 0;
     std::unordered_map<int32_t, int> hmap;
     for (int c = 0; c < nch; ++c) {
@@ -700,10 +710,12 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
             loc = own_n + it->second;
           }
           if (loc < 0 || loc > 65535) return fail(FWI_EINVAL, "chunk too large for 16-bit local indices");
-          m->lconn[(size_t)q * E + e] = (uint16_t)loc;
+          m->lconn[(size_t)q * m->Es + e] = (uint16_t)loc;
         }
       m->ch_halo_ptr[c + 1] = (int)m->halo_ids.size();
       m->L_max = std::max(m->L_max, own_n + (int)hmap.size());
+      m->O_max = std::max(m->O_max, own_n);
+      m->H_max = std::max(m->H_max, (int)hmap.size());
     }
   }
   for (int e = 0; e < E; ++e)
@@ -799,7 +811,8 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
   }
   // device geometry
   const int NG = d == 2 ? 3 : 6;
-  std::vector<float> geo((size_t)NG * E), lgeo((size_t)d * d * (E - m->E0));
+  const size_t Es = (size_t)m->Es;
+  std::vector<float> geo((size_t)NG * Es + 32, 0.f), lgeo((size_t)d * d * (E - m->E0));
   for (int e = 0; e < E; ++e) {
     const double* Ji = &m->Jinv[(size_t)e * d * d];
     const double det = m->detJ[e];
@@ -811,12 +824,12 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
         Gm[r * d + c] = det * s;  // |J| J^-1 J^-T
       }
     if (d == 2) {
-      geo[0 * (size_t)E + e] = (float)Gm[0];
-      geo[1 * (size_t)E + e] = (float)Gm[1];
-      geo[2 * (size_t)E + e] = (float)Gm[3];
+      geo[0 * Es + e] = (float)Gm[0];
+      geo[1 * Es + e] = (float)Gm[1];
+      geo[2 * Es + e] = (float)Gm[3];
     } else {
       const int idx[6] = {0, 1, 2, 4, 5, 8};
-      for (int g = 0; g < 6; ++g) geo[(size_t)g * E + e] = (float)Gm[idx[g]];
+      for (int g = 0; g < 6; ++g) geo[(size_t)g * Es + e] = (float)Gm[idx[g]];
     }
     if (e >= m->E0)
       for (int c = 0; c < d * d; ++c) lgeo[(size_t)c * (E - m->E0) + (e - m->E0)] = (float)(det * Ji[c]);
@@ -922,6 +935,17 @@ int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, doubl
   if (xhat) std::memcpy(xhat, el.xhat.data(), el.xhat.size() * sizeof(double));
   if (w) std::memcpy(w, el.w.data(), el.w.size() * sizeof(double));
   if (dhat) std::memcpy(dhat, el.dhat.data(), el.dhat.size() * sizeof(double));
+  return 0;
+}
+
+int fwi_reference_element_f32(int dim, int k, float* dhat, float* w) {
+  kmvtab::Element el;
+  std::string err;
+  if (!kmvtab::build(dim, k, el, err)) return fail(FWI_EINVAL, "KMV tabulation: " + err);
+  std::vector<float> dh, ww;
+  kmvtab::fp32_tables(el, dh, ww);
+  if (dhat) std::memcpy(dhat, dh.data(), dh.size() * sizeof(float));
+  if (w) std::memcpy(w, ww.data(), ww.size() * sizeof(float));
   return 0;
 }
 
@@ -1136,6 +1160,7 @@ StepArgs base_args(fwi_batch* b) {
   StepArgs a;
   std::memset(&a, 0, sizeof a);
   a.E = m->E;
+  a.Es = m->Es;
   a.E0 = m->E0;
   a.S = b->S;
   a.log2S = b->log2S;
@@ -1148,6 +1173,8 @@ StepArgs base_args(fwi_batch* b) {
     a.ch0 = 0;
     a.N_own = m->N_own;
     a.L_max = m->L_max;
+    a.O_max = m->O_max;
+    a.H_max = m->H_max;
     a.PE = m->P;
     a.SG = std::min(b->S, 4);
     a.tc = m->use_tc ? 1 : 0;

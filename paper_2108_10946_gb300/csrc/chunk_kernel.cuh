@@ -114,7 +114,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     int lq[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
-      lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
+      lq[q] = __ldg(a.lconn + (size_t)q * a.Es + e);
       if constexpr (ROLL || ROLL3) lqs[q * nth + tid] = lq[q];
     }
     const int lb = nsh + el * NI;  // local index of the first bubble node
@@ -133,7 +133,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
     }
     float G[NG];
 #pragma unroll
-    for (int g = 0; g < NG; ++g) G[g] = __ldg(a.geo + (size_t)g * a.E + e);
+    for (int g = 0; g < NG; ++g) G[g] = __ldg(a.geo + (size_t)g * a.Es + e);
     float Am[D * D];
     const int El = a.E - a.E0;
 #pragma unroll

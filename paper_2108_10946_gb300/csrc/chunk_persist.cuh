@@ -1,0 +1,378 @@
+// Persistent, pipelined chunk kernel for triangles without damping-layer elements, batches
+// of S >= 4 shots (work item = one chunk x four shots).
+//
+// Each CTA (256 threads, two per SM) walks a fixed list of work items. While it computes one
+// chunk, the reads of the next ones are already in flight as asynchronous copies:
+//
+//   iteration i:  wait for every copy issued in iteration i-1; barrier
+//                 issue  data of item i+1   (u, v, c^2, c1..c3, Ghat, local connectivity,
+//                                            source/receiver flags; halo DoFs through the
+//                                            halo ids of item i+1)       -> buffer (i+1)%2
+//                        halo ids of item i+2 (needs its descriptor)      -> meta slot (i+2)%4
+//                        descriptor of item i+3                           -> meta slot (i+3)%4
+//                 element phase of item i (buffer i%2), barrier
+//                 update of the owned DoFs, halo sums to the global accumulator, barrier
+//
+// so a chunk's global reads are hidden behind the previous chunk's arithmetic; the only
+// waits are cp.async group waits on the CTA's own copies and __syncthreads.
+//
+// Element phase: two threads per (element, shot), one per reference direction d. Thread d
+// streams row q of Dhat_d (shared memory), forms g_d = (Dhat_d u)_q, swaps it with its
+// partner (shuffle) to have grad u at node q, forms f_d = w_q c_q^2 (Ghat grad u)_d and adds
+// Dhat_d[q][:] f_d to its partial y; the two partial y are summed by shuffles at the end
+// (Section 3.2: the stiffness action sum_q w_q c^2 (J^-T grad phi_i . J^-T grad u)(x_q) with the
+// quadrature points at the nodes). Holding one row instead of two keeps a thread under 128
+// registers.
+//
+// Table layouts in shared memory are DoF-major with the four shots contiguous ([L][4]), so
+// that one 16-byte copy moves a DoF's four shots and the update phase works on float4.
+#pragma once
+#include "chunk_kernel.cuh"
+
+namespace fwi {
+
+constexpr int PT_THREADS = 256;  // 32 elements x 4 shots x 2 directions
+constexpr int PT_PE = 32;        // elements per chunk (triangles)
+constexpr int PT_SG = 4;         // shots per work item
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+__host__ __device__ inline uint32_t pt_al16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Byte offsets of the persistent kernel's dynamic shared memory.
+struct PtLayout {
+  uint32_t rows, rows_dstride;  // Dhat rows [2][NN][NNP] floats; direction stride (floats)
+  uint32_t y, g;                // accumulators [Lmax][4] and [Lmax]
+  uint32_t meta0, meta_stride;  // 4 slots: descriptor (8 ints) + halo ids [Hmax]
+  uint32_t buf0, buf_stride;    // 2 buffers
+  uint32_t bu, bF, bc2, bcv, bv, bcf, bcf_stride, bgeo, binj, blq;  // inside a buffer
+  uint32_t total;
+};
+
+template <int NN, int NS>
+__host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax, bool grad) {
+  constexpr int NNP = (NN + 3) / 4 * 4;
+  PtLayout L{};
+  uint32_t o = 0;
+  L.rows = o;
+  // the second direction's rows start 16 bytes past a bank-aligned offset, so that the two
+  // rows a warp reads at once (one per direction) sit in different banks
+  L.rows_dstride = (uint32_t)(NN * NNP + 4);
+  o += pt_al16(4u * (2u * L.rows_dstride));
+  L.y = o;
+  o += pt_al16(16u * (uint32_t)Lmax);
+  L.g = o;
+  if (grad) o += pt_al16(4u * (uint32_t)Lmax);
+  L.meta0 = o;
+  L.meta_stride = pt_al16(32u + 4u * (uint32_t)Hmax);
+  o += 4u * L.meta_stride;
+  uint32_t b = 0;
+  L.bu = b;
+  b += pt_al16(16u * (uint32_t)Lmax);
+  L.bF = b;
+  if (grad) b += pt_al16(16u * (uint32_t)Lmax);
+  L.bc2 = b;
+  b += pt_al16(4u * (uint32_t)Lmax);
+  L.bcv = b;
+  if (grad) b += pt_al16(4u * (uint32_t)Lmax);
+  L.bv = b;
+  b += pt_al16(16u * (uint32_t)Omax);
+  L.bcf = b;
+  L.bcf_stride = pt_al16(4u * (uint32_t)Omax);
+  b += 3u * L.bcf_stride;
+  L.bgeo = b;
+  b += 3u * PT_PE * 4u;
+  L.binj = b;
+  b += PT_PE * 4u;
+  L.blq = b;
+  b += pt_al16((uint32_t)NS * PT_PE * 2u);
+  L.buf_stride = pt_al16(b);
+  L.buf0 = o;
+  o += 2u * L.buf_stride;
+  L.total = o;
+  return L;
+}
+
+// Work item w of a launch over chunks [ch0, ch0 + nch): chunk ch0 + w / ngrp, shots
+// [4 (w % ngrp), 4 (w % ngrp) + 4).
+struct PtItem {
+  int c, s0;
+  bool valid;
+};
+
+__device__ __forceinline__ PtItem pt_item(const StepArgs& a, int i, int nwork, int ngrp) {
+  PtItem it;
+  const int w = blockIdx.x + i * gridDim.x;
+  it.valid = w < nwork;
+  it.c = a.ch0 + (it.valid ? w / ngrp : 0);
+  it.s0 = it.valid ? (w % ngrp) * PT_SG : 0;
+  return it;
+}
+
+// descriptor of item i: chunk fields e0, ne, own_lo, own_n, nsh, hp and the next chunk's hp
+__device__ __forceinline__ void pt_issue_desc(const StepArgs& a, const PtLayout& L, char* sm,
+                                              int i, int nwork, int ngrp) {
+  const PtItem it = pt_item(a, i, nwork, ngrp);
+  if (!it.valid) return;
+  int* desc = reinterpret_cast<int*>(sm + L.meta0 + (i & 3) * L.meta_stride);
+  const int t = threadIdx.x;
+  if (t < 6) cp_async4(desc + t, a.chunks + 6 * it.c + t);
+  if (t == 6) cp_async4(desc + 6, a.chunks + 6 * (it.c + 1) + 5);
+}
+
+__device__ __forceinline__ void pt_issue_halo(const StepArgs& a, const PtLayout& L, char* sm,
+                                              int i, int nwork, int ngrp) {
+  const PtItem it = pt_item(a, i, nwork, ngrp);
+  if (!it.valid) return;
+  char* meta = sm + L.meta0 + (i & 3) * L.meta_stride;
+  const int* desc = reinterpret_cast<const int*>(meta);
+  int* ids = reinterpret_cast<int*>(meta + 32);
+  const int hp = desc[5], hn = desc[6] - desc[5];
+  for (int h = threadIdx.x; h < hn; h += PT_THREADS) cp_async4(ids + h, a.halo + hp + h);
+}
+
+template <int NS, bool GRAD>
+__device__ __forceinline__ void pt_issue_data(const StepArgs& a, const PtLayout& L, char* sm, int i,
+                                              int nwork, int ngrp) {
+  const PtItem it = pt_item(a, i, nwork, ngrp);
+  if (!it.valid) return;
+  const char* meta = sm + L.meta0 + (i & 3) * L.meta_stride;
+  const int* desc = reinterpret_cast<const int*>(meta);
+  const int* ids = reinterpret_cast<const int*>(meta + 32);
+  char* B = sm + L.buf0 + (i & 1) * L.buf_stride;
+  const int e0 = desc[0], own_lo = desc[2], own_n = desc[3], hn = desc[6] - desc[5];
+  const int S = a.S, s0 = it.s0, t = threadIdx.x;
+  float* bu = reinterpret_cast<float*>(B + L.bu);
+  float* bF = reinterpret_cast<float*>(B + L.bF);
+  float* bv = reinterpret_cast<float*>(B + L.bv);
+  float* bc2 = reinterpret_cast<float*>(B + L.bc2);
+  float* bcv = reinterpret_cast<float*>(B + L.bcv);
+  for (int l = t; l < own_n; l += PT_THREADS) {
+    const size_t gi = (size_t)(own_lo + l) * S + s0;
+    cp_async16(bu + 4 * l, a.u + gi);
+    cp_async16(bv + 4 * l, a.v + gi);
+    if (GRAD) cp_async16(bF + 4 * l, a.ring_u + gi);
+    const size_t dof = (size_t)(own_lo + l);
+    cp_async4(bc2 + l, a.c2 + dof);
+    if (GRAD) cp_async4(bcv + l, a.cvel + dof);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      cp_async4(reinterpret_cast<float*>(B + L.bcf + r * L.bcf_stride) + l, a.cf + (size_t)r * a.N + dof);
+  }
+  for (int h = t; h < hn; h += PT_THREADS) {
+    const int id = ids[h];
+    const size_t gi = (size_t)id * S + s0;
+    cp_async16(bu + 4 * (own_n + h), a.u + gi);
+    if (GRAD) cp_async16(bF + 4 * (own_n + h), a.ring_u + gi);
+    cp_async4(bc2 + own_n + h, a.c2 + id);
+    if (GRAD) cp_async4(bcv + own_n + h, a.cvel + id);
+  }
+  // per-element arrays of the chunk's 32 elements (rows padded to a multiple of 32 elements,
+  // e0 a multiple of 32 for chunks without layer elements: whole 16-byte groups)
+  if (t < 24) {
+    const int g = t >> 3, part = t & 7;
+    cp_async16(B + L.bgeo + (g * PT_PE + part * 4) * 4, a.geo + (size_t)g * a.Es + e0 + part * 4);
+  } else if (t < 32) {
+    const int part = t - 24;
+    cp_async16(B + L.binj + part * 16, a.inj + e0 + part * 4);
+  } else if (t < 32 + 4 * NS) {
+    const int q = (t - 32) >> 2, part = (t - 32) & 3;
+    cp_async16(B + L.blq + (q * PT_PE + part * 8) * 2, a.lconn + (size_t)q * a.Es + e0 + part * 8);
+  }
+}
+
+template <int NN, int NS, int MODE>
+__device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) {
+  constexpr int NI = NN - NS;
+  constexpr int NNP = (NN + 3) / 4 * 4;
+  constexpr bool ROLL = NN >= 16;
+  constexpr bool GRAD = MODE == 2;
+  constexpr bool ADJ = MODE != 0;
+  static_assert(MODE != 2, "the gradient steps use the chunk kernel");
+  const int ngrp = a.S / PT_SG;
+  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max, GRAD);
+  const int t = threadIdx.x;
+  float* rows = reinterpret_cast<float*>(sm + L.rows);
+  float4* Y4 = reinterpret_cast<float4*>(sm + L.y);
+  float* Y = reinterpret_cast<float*>(sm + L.y);
+
+  // Dhat rows (once per CTA) and a zero accumulator table
+  for (int idx = t; idx < 2 * (int)L.rows_dstride; idx += PT_THREADS) {
+    const int d = idx / (int)L.rows_dstride, rem = idx - d * (int)L.rows_dstride;
+    const int q = rem / NNP, j = rem - q * NNP;
+    rows[idx] = (q < NN && j < NN) ? c_dhat[(d * NN + q) * NN + j] : 0.f;
+  }
+  for (int l = t; l < a.L_max; l += PT_THREADS) Y4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  // prologue: descriptors of items 0, 1; halo ids of 0, 1 and descriptor of 2; data of 0
+  pt_issue_desc(a, L, sm, 0, nwork, ngrp);
+  pt_issue_desc(a, L, sm, 1, nwork, ngrp);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  pt_issue_halo(a, L, sm, 0, nwork, ngrp);
+  pt_issue_halo(a, L, sm, 1, nwork, ngrp);
+  pt_issue_desc(a, L, sm, 2, nwork, ngrp);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  pt_issue_data<NS, GRAD>(a, L, sm, 0, nwork, ngrp);
+  cp_async_commit();
+
+  const int d = t & 1, es = t >> 1, el = es & (PT_PE - 1), sl = es >> 5;
+  bool bad = false;
+  for (int i = 0;; ++i) {
+    const PtItem it = pt_item(a, i, nwork, ngrp);
+    if (!it.valid) break;
+    cp_async_wait<0>();
+    __syncthreads();
+    pt_issue_data<NS, GRAD>(a, L, sm, i + 1, nwork, ngrp);
+    pt_issue_halo(a, L, sm, i + 2, nwork, ngrp);
+    pt_issue_desc(a, L, sm, i + 3, nwork, ngrp);
+    cp_async_commit();
+
+    const char* meta = sm + L.meta0 + (i & 3) * L.meta_stride;
+    const int* desc = reinterpret_cast<const int*>(meta);
+    const int* ids = reinterpret_cast<const int*>(meta + 32);
+    const int e0 = desc[0], ne = desc[1], own_lo = desc[2], own_n = desc[3], nsh = desc[4];
+    const int hn = desc[6] - desc[5];
+    const char* B = sm + L.buf0 + (i & 1) * L.buf_stride;
+    const float* bu = reinterpret_cast<const float*>(B + L.bu);
+    const float* bc2 = reinterpret_cast<const float*>(B + L.bc2);
+    const float* bgeo = reinterpret_cast<const float*>(B + L.bgeo);
+    const int* binj = reinterpret_cast<const int*>(B + L.binj);
+    const unsigned short* blq = reinterpret_cast<const unsigned short*>(B + L.blq);
+
+    // ---- element phase ------------------------------------------------------------------
+    {
+      const bool act = el < ne;
+      const int e = e0 + el, s = it.s0 + sl;
+      const int lb = nsh + el * NI;
+      float U[NNP], y[NNP];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) U[q] = bu[4 * (act ? (int)blq[q * PT_PE + el] : 0) + sl];
+#pragma unroll
+      for (int j = 0; j < NI; ++j) U[NS + j] = act ? bu[4 * (lb + j) + sl] : 0.f;
+#pragma unroll
+      for (int j = NN; j < NNP; ++j) U[j] = 0.f;
+#pragma unroll
+      for (int j = 0; j < NNP; ++j) y[j] = 0.f;
+      const float G0 = bgeo[el], G1 = bgeo[PT_PE + el], G2 = bgeo[2 * PT_PE + el];
+      // f_d = Ga * (grad u)_x + Gb * (grad u)_z with Ghat = [[G0, G1], [G1, G2]]
+      const float Ga = act ? (d ? G1 : G0) : 0.f, Gb = act ? (d ? G2 : G1) : 0.f;
+      const int slot = act ? binj[el] : -1;
+      if (!ADJ && slot >= 0 && d == 0 && a.rec != nullptr) {
+        const int rb = __ldg(a.rslot_ptr + slot), re = __ldg(a.rslot_ptr + slot + 1);
+        for (int r = rb; r < re; ++r) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < NN; ++k) acc = fmaf(__ldg(a.rslot_phi + (size_t)r * NN + k), U[k], acc);
+          a.rec[((size_t)s * (a.nt + 1) + a.n) * a.R + __ldg(a.rslot_rec + r)] = acc;
+        }
+      }
+      const float* rowd = rows + d * L.rows_dstride;
+#pragma unroll(ROLL ? 1 : NN)
+      for (int q = 0; q < NN; ++q) {
+        float r[NNP];
+#pragma unroll
+        for (int j = 0; j < NNP; j += 4) {
+          const float4 r4 = *reinterpret_cast<const float4*>(rowd + q * NNP + j);
+          r[j] = r4.x;
+          r[j + 1] = r4.y;
+          r[j + 2] = r4.z;
+          r[j + 3] = r4.w;
+        }
+        const int lqq = q < NS ? (act ? (int)blq[q * PT_PE + el] : 0) : (act ? lb + (q - NS) : 0);
+        const float wc = c_w[q] * bc2[lqq];
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < NNP; j += 4) {
+          acc0 = ffma2(make_float2(r[j], r[j + 1]), make_float2(U[j], U[j + 1]), acc0);
+          acc1 = ffma2(make_float2(r[j + 2], r[j + 3]), make_float2(U[j + 2], U[j + 3]), acc1);
+        }
+        const float gd = (acc0.x + acc1.x) + (acc0.y + acc1.y);
+        const float go = __shfl_xor_sync(0xffffffffu, gd, 1);
+        const float gx = d ? go : gd, gz = d ? gd : go;
+        const float f = wc * (Ga * gx + Gb * gz);
+#pragma unroll
+        for (int j = 0; j < NNP; j += 2) {
+          const float2 yy = ffma2(make_float2(r[j], r[j + 1]), make_float2(f, f), make_float2(y[j], y[j + 1]));
+          y[j] = yy.x;
+          y[j + 1] = yy.y;
+        }
+      }
+      // sources (forward) and adjoint sources at the receivers, in direction 0's partial sum
+      if (slot >= 0 && d == 0) {
+        if (!ADJ) {
+          if (__ldg(a.src_elem + s) == e) {
+            const float wv = __ldg(a.wavelet + (size_t)s * a.nt + a.n);
+#pragma unroll
+            for (int k = 0; k < NN; ++k) y[k] -= wv * __ldg(a.src_phi + (size_t)s * NN + k);
+          }
+        } else {
+          const int rb = __ldg(a.rslot_ptr + slot), re = __ldg(a.rslot_ptr + slot + 1);
+          for (int r = rb; r < re; ++r) {
+            const float res = __ldg(a.resid + ((size_t)s * (a.nt + 1) + a.n) * a.R + __ldg(a.rslot_rec + r));
+#pragma unroll
+            for (int k = 0; k < NN; ++k) y[k] = fmaf(res, __ldg(a.rslot_phi + (size_t)r * NN + k), y[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NN; ++k) y[k] += __shfl_xor_sync(0xffffffffu, y[k], 1);
+      if (act) {
+        if (d == 0) {
+#pragma unroll
+          for (int q = 0; q < NS; ++q) atomicAdd(Y + 4 * (int)blq[q * PT_PE + el] + sl, y[q]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NI; ++j) Y[4 * (lb + j) + sl] = y[NS + j];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- owned DoFs: increment update; halo DoFs: sums to the global accumulator ----------
+    {
+      const float4* bu4 = reinterpret_cast<const float4*>(B + L.bu);
+      const float4* bv4 = reinterpret_cast<const float4*>(B + L.bv);
+      const float* cf1 = reinterpret_cast<const float*>(B + L.bcf);
+      const float* cf2 = reinterpret_cast<const float*>(B + L.bcf + L.bcf_stride);
+      const float* cf3 = reinterpret_cast<const float*>(B + L.bcf + 2 * L.bcf_stride);
+      const int S = a.S;
+      for (int l = t; l < own_n; l += PT_THREADS) {
+        const float4 yv = Y4[l], uo = bu4[l], vo = bv4[l];
+        Y4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float c1 = cf1[l], c2 = cf2[l], c3 = cf3[l];
+        float4 vn, un;
+        vn.x = c1 * vo.x - c2 * yv.x - c3 * uo.x;
+        vn.y = c1 * vo.y - c2 * yv.y - c3 * uo.y;
+        vn.z = c1 * vo.z - c2 * yv.z - c3 * uo.z;
+        vn.w = c1 * vo.w - c2 * yv.w - c3 * uo.w;
+        un.x = uo.x + vn.x;
+        un.y = uo.y + vn.y;
+        un.z = uo.z + vn.z;
+        un.w = uo.w + vn.w;
+        const size_t gi = (size_t)(own_lo + l) * S + it.s0;
+        *reinterpret_cast<float4*>(a.v + gi) = vn;
+        *reinterpret_cast<float4*>(a.u + gi) = un;
+        bad |= !(isfinite(un.x) && isfinite(un.y) && isfinite(un.z) && isfinite(un.w));
+      }
+      for (int h = t; h < hn; h += PT_THREADS) {
+        const float4 yv = Y4[own_n + h];
+        Y4[own_n + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        atomicAdd(reinterpret_cast<float4*>(a.r + (size_t)(ids[h] - a.N_own) * S + it.s0), yv);
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if (bad) atomicOr(a.status, 1);
+}
+
+}  // namespace fwi

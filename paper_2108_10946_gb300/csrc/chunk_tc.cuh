@@ -183,9 +183,9 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
     for (int cc = 0; cc < D * D; ++cc) Am[cc] = 0.f;
     if (valid) {
 #pragma unroll
-      for (int q = 0; q < NS; ++q) lq[q] = __ldg(a.lconn + (size_t)q * a.E + e);
+      for (int q = 0; q < NS; ++q) lq[q] = __ldg(a.lconn + (size_t)q * a.Es + e);
 #pragma unroll
-      for (int g = 0; g < 3; ++g) Gm[g] = __ldg(a.geo + (size_t)g * a.E + e);
+      for (int g = 0; g < 3; ++g) Gm[g] = __ldg(a.geo + (size_t)g * a.Es + e);
       if (layer) {
         const int El = a.E - a.E0;
 #pragma unroll

@@ -10,8 +10,8 @@ namespace fwi {
 // element read one contiguous run of S floats):
 //   wavefields u, v (increment), r (shared-DoF accumulator)       [N][S]
 //   element-interior DoF j of element e has global id Ns + e*NI + j (no connectivity)
-//   conn   [NS][E]  shared-node DoF ids (node-major, coalesced over elements)
-//   geo    [NG][E]  Ghat = |J| J^-1 J^-T (NG = 3 in 2D, 6 in 3D: xx, xy, yy / xx, xy, xz, yy,
+//   conn   [NS][E]  shared-node DoF ids (node-major, coalesced over elements; plain layout)
+//   geo    [NG][Es] Ghat = |J| J^-1 J^-T (NG = 3 in 2D, 6 in 3D: xx, xy, yy / xx, xy, xz, yy,
 //                   yz, zz)
 //   lgeo   [D*D][Elayer]  A = |J| J^-1 (row-major) for the damping-layer elements
 //                   e >= E0 (indexed e - E0)
@@ -19,15 +19,18 @@ namespace fwi {
 //   P, Pacc          [Nl][D][S], Y / Yacc [Nl][S] (3D)
 struct StepArgs {
   int E, E0, S, Ns, N;
+  int Es;              // row stride of the element arrays geo, lconn and inj: E rounded up to a
+                       // multiple of 32 (16-byte aligned rows for vector and cp.async loads)
   int log2S;
   int h0, hcnt;        // node kernel range: DoFs [h0, h0 + hcnt), r indexed from h0
   // chunked layout (layout 0)
+  int O_max, H_max;    // largest owned-DoF range and halo list of a chunk
   int nch, nch0, ch0, N_own, L_max, PE, SG;  // chunks, owned DoFs, largest chunk table, elements per
                                   // chunk, shots per CTA
   const int* bub;            // [E] first bubble DoF of each element
   const int* chunks;         // [nch][6]: e0, ne, own_lo, own_n, nsh, halo_ptr
   const int* halo;           // halo DoF ids, chunk by chunk
-  const unsigned short* lconn;  // [NS][E] chunk-local index of each shared node
+  const unsigned short* lconn;  // [NS][Es] chunk-local index of each shared node
   int tc;              // chunked layout, 2D: element contraction on the tensor cores
   int mode;            // 0 forward, 1 adjoint (with gradient when ring != null)
   int n;               // time index (forward: step n -> n+1; adjoint: step m)
@@ -50,7 +53,7 @@ struct StepArgs {
   float* Yacc;
   float* PaccY;        // 3D forward: lumped gradient of Y (D_{omega,3} term)
   // sources / receivers
-  const int* inj;          // [E] slot id or -1
+  const int* inj;          // [Es] slot id or -1 (padding -1)
   const int* src_elem;     // [S]
   const float* src_phi;    // [S][NN]
   const float* wavelet;    // [S][nt]
@@ -97,5 +100,6 @@ void launch_finish_gradient(const double* gsum, const double* gcomp, const float
                             cudaStream_t st);
 void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st);
 void launch_residual(const float* d, const float* obs, float* res, int64_t n, cudaStream_t st);
+int measure_fma_peak(double* tflops, int* sms);
 
 }  // namespace fwi

@@ -28,6 +28,7 @@ __constant__ float c_w[NN];
 #include "chunk_kernel.cuh"
 #if KMV_DIM == 2
 #include "chunk_tc.cuh"
+#include "chunk_persist.cuh"
 #endif
 
 namespace fwi {
@@ -106,6 +107,47 @@ int launch_chunk_tc_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
 
 #endif
 
+#if KMV_DIM == 2
+template <int MODE>
+__global__ void __launch_bounds__(PT_THREADS, 2) k_chunk_pt(const StepArgs a, int nwork) {
+  extern __shared__ __align__(16) char smem_pt[];
+  pt_body<NN, NS, MODE>(a, smem_pt, nwork);
+}
+
+// Persistent pipelined kernel over chunks [ch0, ch0 + nch) (no layer elements), S a
+// multiple of 4. Returns -1 (nothing launched) when its shared-memory tables do not fit, a
+// cudaError_t on failure, 0 once launched.
+template <int MODE>
+int launch_chunk_pt_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
+  if (nch <= 0) return 0;
+  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max, MODE == 2);
+  if (L.total > 227u * 1024u) return -1;
+  static size_t configured[64] = {0};
+  static int per_sm[64] = {0}, nsm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  if (L.total > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_pt<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.total);
+    if (e != cudaSuccess) return (int)e;
+    configured[dev] = L.total;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[dev], k_chunk_pt<MODE>, PT_THREADS,
+                                                      L.total);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+  }
+  if (per_sm[dev] < 1) return -1;
+  const int nwork = nch * (a.S / PT_SG);
+  StepArgs b = a;
+  b.ch0 = ch0;
+  const int grid = std::min(nwork, per_sm[dev] * nsm[dev]);
+  k_chunk_pt<MODE><<<grid, PT_THREADS, L.total, st>>>(b, nwork);
+  return 0;
+}
+#endif
+
 // chunks [0, nch0) hold no damping-layer element, chunks [nch0, nch) do
 int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
   const int mode = a.mode == 0 ? 0 : (a.ring_u != nullptr ? 2 : 1);
@@ -122,6 +164,20 @@ int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
         if (!rc) rc = launch_chunk_tc_t<2, true>(a, a.nch0, a.nch - a.nch0, stl);
     }
     return rc;
+  }
+#endif
+#if KMV_DIM == 2
+  // triangles, four shots per work item: the persistent kernel takes the chunks without
+  // layer elements in the forward steps and the first adjoint step (the gradient steps use
+  // the chunk kernel)
+  if (mode != 2 && a.S % PT_SG == 0 && a.nch0 > 0) {
+    rc = mode == 0 ? launch_chunk_pt_t<0>(a, 0, a.nch0, st) : launch_chunk_pt_t<1>(a, 0, a.nch0, st);
+    if (rc > 0) return rc;
+    if (rc == 0) {
+      if (mode == 0) return launch_chunk_t<0, true>(a, a.nch0, a.nch - a.nch0, stl);
+      return launch_chunk_t<1, true>(a, a.nch0, a.nch - a.nch0, stl);
+    }
+    rc = 0;  // the tables do not fit: the chunk kernel below takes every chunk
   }
 #endif
   switch (mode) {

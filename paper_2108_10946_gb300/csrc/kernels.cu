@@ -1,5 +1,7 @@
 // Dimension-generic kernels: the shared-DoF update, the FP64 compensated gradient fold,
 // the final M^-1 scaling and mask of Eq. (gradient3), and the misfit reduction.
+#include <algorithm>
+
 #include "update.cuh"
 
 namespace fwi {
@@ -99,6 +101,65 @@ __global__ void residual_kernel(const float* __restrict__ d, const float* __rest
 void launch_residual(const float* d, const float* obs, float* res, int64_t n, cudaStream_t st) {
   if (n == 0) return;
   residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, obs, res, n);
+}
+
+// FP32 FMA throughput probe: every thread runs 16 independent packed FP32x2 FMA chains
+// (the instruction the element kernels use), so that the FMA pipes, not latency, bound it.
+// Each ffma2 is two fused multiply-adds, four flops.
+__global__ void __launch_bounds__(256) fma_peak_kernel(float* out, int iters, float a) {
+  float2 acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = make_float2(threadIdx.x * 1e-3f + c, c * 0.5f);
+  const float2 m = make_float2(a, a), b = make_float2(1e-7f, -1e-7f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      unsigned long long r;
+      asm volatile("fma.rn.f32x2 %0, %1, %2, %3;"
+                   : "=l"(r)
+                   : "l"(*reinterpret_cast<const unsigned long long*>(&acc[c])),
+                     "l"(*reinterpret_cast<const unsigned long long*>(&m)),
+                     "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+      acc[c] = *reinterpret_cast<float2*>(&r);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) s += acc[c].x + acc[c].y;
+  if (s == 12345.678f) out[blockIdx.x] = s;  // keeps the chains live
+}
+
+int measure_fma_peak(double* tflops, int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  int nsm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return (int)e;
+  float* out = nullptr;
+  if ((e = cudaMalloc(&out, sizeof(float) * 4096)) != cudaSuccess) return (int)e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = nsm * 8, threads = 256, iters = 4096;
+  fma_peak_kernel<<<blocks, threads>>>(out, 64, 0.999f);  // warm-up
+  double best = 0;
+  for (int rep = 0; rep < 5; ++rep) {
+    cudaEventRecord(e0);
+    fma_peak_kernel<<<blocks, threads>>>(out, iters, 0.999f);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = (double)blocks * threads * iters * 16 * 4;
+    if (ms > 0) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (tflops) *tflops = best;
+  if (sms) *sms = nsm;
+  return (int)e;
 }
 
 void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st) {

@@ -396,6 +396,152 @@ bool solve_orbits(const std::string& kinds, const std::vector<ld>& fixed,
 
 }  // namespace
 
+namespace {
+// Solves the small dense system M z = r (M square, order m) by Gaussian elimination with
+// partial pivoting in long double; a tiny ridge keeps a rank-deficient M solvable.
+void dense_solve(std::vector<ld> M, std::vector<ld> r, int m, std::vector<ld>& z) {
+  ld tr = 0;
+  for (int i = 0; i < m; ++i) tr += std::fabs(M[i * m + i]);
+  for (int i = 0; i < m; ++i) M[i * m + i] += 1e-28L * (tr + 1e-300L);
+  for (int c = 0; c < m; ++c) {
+    int p = c;
+    for (int i = c + 1; i < m; ++i)
+      if (std::fabs(M[i * m + c]) > std::fabs(M[p * m + c])) p = i;
+    if (p != c) {
+      for (int j = 0; j < m; ++j) std::swap(M[c * m + j], M[p * m + j]);
+      std::swap(r[c], r[p]);
+    }
+    const ld d = M[c * m + c];
+    if (d == 0) continue;
+    for (int i = c + 1; i < m; ++i) {
+      const ld f = M[i * m + c] / d;
+      if (f == 0) continue;
+      for (int j = c; j < m; ++j) M[i * m + j] -= f * M[c * m + j];
+      r[i] -= f * r[c];
+    }
+  }
+  z.assign(m, 0);
+  for (int i = m - 1; i >= 0; --i) {
+    ld s = r[i];
+    for (int j = i + 1; j < m; ++j) s -= M[i * m + j] * z[j];
+    z[i] = M[i * m + i] != 0 ? s / M[i * m + i] : 0;
+  }
+}
+
+// Rounds x[n] to FP32 values x32 that keep the linear identities A x = b (A: m x n row-major,
+// exact for x in FP64) as closely as possible. The entries are rounded one at a time, from the
+// largest FP32 spacing (ulp) to the smallest; before each rounding, the entries not yet
+// rounded receive the minimum-norm correction that cancels the residual left by those already
+// rounded, so that the finely spaced entries absorb what the coarse ones could not represent.
+void round_keeping(const std::vector<ld>& x0, const std::vector<ld>& A, const std::vector<ld>& b,
+                   int m, float* out) {
+  const int n = (int)x0.size();
+  std::vector<ld> x(x0);
+  std::vector<int> order(n);
+  std::vector<ld> sp(n);
+  for (int j = 0; j < n; ++j) {
+    order[j] = j;
+    const float f = (float)x0[j];
+    sp[j] = (ld)std::nextafter(std::fabs(f), INFINITY) - (ld)std::fabs(f);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return sp[a] > sp[c]; });
+  std::vector<char> fixed(n, 0);
+  std::vector<ld> val(n, 0);
+  for (int k = 0; k < n; ++k) {
+    const int j = order[k];
+    // residual with the rounded entries at their FP32 values and the rest at their targets
+    std::vector<ld> r(m, 0);
+    for (int i = 0; i < m; ++i) {
+      ld s = -b[i];
+      for (int c = 0; c < n; ++c) s += A[(size_t)i * n + c] * (fixed[c] ? val[c] : x[c]);
+      r[i] = s;
+    }
+    std::vector<int> fr;
+    for (int c = 0; c < n; ++c)
+      if (!fixed[c]) fr.push_back(c);
+    const int nf = (int)fr.size();
+    std::vector<ld> corr(nf, 0);
+    if (nf > m) {  // minimum-norm correction: corr = -A_f^T (A_f A_f^T)^-1 r
+      std::vector<ld> M((size_t)m * m, 0), z;
+      for (int i = 0; i < m; ++i)
+        for (int i2 = 0; i2 < m; ++i2) {
+          ld s = 0;
+          for (int c : fr) s += A[(size_t)i * n + c] * A[(size_t)i2 * n + c];
+          M[(size_t)i * m + i2] = s;
+        }
+      dense_solve(M, r, m, z);
+      for (int t = 0; t < nf; ++t) {
+        ld s = 0;
+        for (int i = 0; i < m; ++i) s += A[(size_t)i * n + fr[t]] * z[i];
+        corr[t] = -s;
+      }
+    } else {  // least squares: (A_f^T A_f) corr = -A_f^T r
+      std::vector<ld> M((size_t)nf * nf, 0), rhs(nf, 0), z;
+      for (int t = 0; t < nf; ++t) {
+        for (int t2 = 0; t2 < nf; ++t2) {
+          ld s = 0;
+          for (int i = 0; i < m; ++i) s += A[(size_t)i * n + fr[t]] * A[(size_t)i * n + fr[t2]];
+          M[(size_t)t * nf + t2] = s;
+        }
+        ld s = 0;
+        for (int i = 0; i < m; ++i) s += A[(size_t)i * n + fr[t]] * r[i];
+        rhs[t] = -s;
+      }
+      dense_solve(M, rhs, nf, z);
+      corr = z;
+    }
+    for (int t = 0; t < nf; ++t) x[fr[t]] += corr[t];
+    val[j] = (ld)(float)x[j];
+    fixed[j] = 1;
+  }
+  for (int j = 0; j < n; ++j) out[j] = (float)val[j];
+}
+
+ld mono_at(const int* e, const double* x, int dim) {
+  ld v = 1;
+  for (int d = 0; d < dim; ++d) v *= ipow((ld)x[d], e[d]);
+  return v;
+}
+}  // namespace
+
+void fp32_tables(const Element& el, std::vector<float>& dhat32, std::vector<float>& w32) {
+  const int dim = el.dim, n = el.n;
+  dhat32.assign((size_t)dim * n * n, 0.f);
+  w32.assign(n, 0.f);
+  // derivative rows: d/dx_d of every monomial of degree <= 2 at node q
+  auto e2 = exps_up_to(dim, 2);
+  const int m2 = (int)e2.size();
+  std::vector<ld> A((size_t)m2 * n);
+  for (int i = 0; i < m2; ++i)
+    for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = mono_at(e2[i].data(), &el.xhat[(size_t)j * dim], dim);
+  for (int d = 0; d < dim; ++d)
+    for (int q = 0; q < n; ++q) {
+      std::vector<ld> row(n), b(m2);
+      for (int j = 0; j < n; ++j) row[j] = el.dhat[((size_t)d * n + q) * n + j];
+      for (int i = 0; i < m2; ++i) {
+        const auto& ex = e2[i];
+        if (ex[d] == 0) {
+          b[i] = 0;
+          continue;
+        }
+        int e[3] = {ex[0], ex[1], ex[2]};
+        e[d] -= 1;
+        b[i] = ex[d] * mono_at(e, &el.xhat[(size_t)q * dim], dim);
+      }
+      round_keeping(row, A, b, m2, &dhat32[((size_t)d * n + q) * n]);
+    }
+  // weights: the integrals of 1 and of the coordinates over the reference simplex
+  auto e1 = exps_up_to(dim, 1);
+  const int m1 = (int)e1.size();
+  std::vector<ld> A1((size_t)m1 * n), b1(m1);
+  for (int i = 0; i < m1; ++i) {
+    for (int j = 0; j < n; ++j) A1[(size_t)i * n + j] = mono_at(e1[i].data(), &el.xhat[(size_t)j * dim], dim);
+    b1[i] = mono_integral(e1[i].data(), dim);
+  }
+  std::vector<ld> wv(el.w.begin(), el.w.end());
+  round_keeping(wv, A1, b1, m1, w32.data());
+}
+
 void Element::basis(const double* x, double* phi) const {
   ld X[3] = {0, 0, 0};
   for (int d = 0; d < dim; ++d) X[d] = x[d];

@@ -36,4 +36,10 @@ struct Element {
 // Builds KMVktri (dim 2, k 2..5) or KMVktet (dim 3, k 2..3). Returns false with a message.
 bool build(int dim, int k, Element& out, std::string& err);
 
+// FP32 tables for the kernels: dhat32[dim][n][n] and w32[n], rounded so that the identities
+// every derivative row and the weights satisfy exactly in FP64 still hold as closely as FP32
+// values allow: each row of dhat differentiates the polynomials of degree <= 2 at its node,
+// and the weights integrate degree <= 1 (see kmv_tab.cpp).
+void fp32_tables(const Element& el, std::vector<float>& dhat32, std::vector<float>& w32);
+
 }  // namespace kmvtab

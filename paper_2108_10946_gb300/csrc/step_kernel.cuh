@@ -51,7 +51,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a) {
   for (int j = 0; j < NI; ++j) U[NS + j] = a.u[(size_t)(ib + j) * S + s];
   float G[NG];
 #pragma unroll
-  for (int g = 0; g < NG; ++g) G[g] = __ldg(a.geo + (size_t)g * a.E + e);
+  for (int g = 0; g < NG; ++g) G[g] = __ldg(a.geo + (size_t)g * a.Es + e);
   float Am[D * D];
   const int El = a.E - a.E0;
 #pragma unroll

@@ -61,6 +61,7 @@ def load():
         "fwi_reference_element": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                  _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
         "fwi_get_dt": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+        "fwi_reference_element_f32": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
         "fwi_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
         "fwi_forward_shot": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_adjoint_shot": (ctypes.c_int, [_P, _P, _P]),
@@ -76,6 +77,7 @@ def load():
         "fwi_mesh_free": (ctypes.c_int, [_P]),
         "fwi_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
         "fwi_launch_count": (ctypes.c_int64, []),
+        "fwi_fp32_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,6 +133,24 @@ def reference_element(dim, k):
     _check(lib.fwi_reference_element(dim, k, ctypes.byref(n), _ptr(xh), _ptr(w), _ptr(dh),
                                      ctypes.byref(deg)))
     return xh, w, dh, deg.value
+
+
+def reference_element_f32(dim, k):
+    """(dhat [dim][n][n], w [n]) as the FP32 tables the kernels use (host only)."""
+    xh, _, _, _ = reference_element(dim, k)
+    n = xh.shape[0]
+    dh = np.zeros((dim, n, n), dtype=np.float32)
+    w = np.zeros(n, dtype=np.float32)
+    _check(load().fwi_reference_element_f32(dim, k, _ptr(dh), _ptr(w)))
+    return dh, w
+
+
+def fp32_peak():
+    """(measured FP32 FMA TFLOP/s of the current device, its SM count)."""
+    t = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(load().fwi_fp32_peak(ctypes.byref(t), ctypes.byref(n)))
+    return t.value, n.value
 
 
 def launch_count():

@@ -153,3 +153,34 @@ def test_batch_bytes_counts_every_device_array():
     expect = floats * 4 + 2 * N * 8 + m.E * 4
     assert m.batch_bytes(S, R) == expect
     m.close()
+
+
+@pytest.mark.parametrize("dim,k", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3)])
+def test_fp32_tables_keep_the_polynomial_identities(dim, k):
+    """The kernels' FP32 copies of Dhat and w are not nearest-rounded: every derivative row
+    still differentiates the polynomials of degree <= 2 at its node to within a small
+    fraction of what nearest rounding leaves (that residual is the same in every element and
+    drifts the phase of long records), and the weights still sum to the reference volume.
+    Each entry stays within a few FP32 spacings (of its row's largest entry) of its FP64
+    value."""
+    import numpy as np
+    from oracle import kmv
+    import paper_2108_10946_gb300.lib as L
+    dh32, w32 = L.reference_element_f32(dim, k)
+    xh, w64, dh64, _ = L.reference_element(dim, k)
+    monos = kmv._monomials(dim, 2)
+    A = np.stack([kmv.peval(kmv._mono(e), xh) for e in monos])
+    near = new = 0.0
+    for d in range(dim):
+        for q in range(len(xh)):
+            b = np.array([kmv.pgrad(kmv._mono(e), xh[q:q + 1])[0, d] for e in monos])
+            near = max(near, np.abs(A @ dh64[d, q].astype(np.float32).astype(np.float64) - b).max())
+            new = max(new, np.abs(A @ dh32[d, q].astype(np.float64) - b).max())
+    print(f"dim {dim} k {k}: P2 residual of the FP32 rows {new:.2e} (nearest rounding {near:.2e})")
+    assert new < 3e-8 and new < near / 5
+    # each entry moves by at most a few spacings of the coarsest FP32 value in its row
+    row_ulp = np.spacing(np.abs(dh64).max(axis=2).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(dh32.astype(np.float64) - dh64).max(axis=2) <= 4 * row_ulp)
+    vol = 0.5 if dim == 2 else 1.0 / 6.0
+    assert abs(np.sum(w32.astype(np.float64)) - vol) < 1e-10
+    assert np.abs(w32.astype(np.float64) - w64).max() <= 4 * np.abs(w64.astype(np.float32) - w64).max() + 1e-12
