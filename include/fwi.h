@@ -53,7 +53,7 @@ typedef struct fwi_batch fwi_batch;
  *                    2dels and 3dels; k = 1 is excluded: Table gwpl shows it does not reach
  *                    the error threshold).
  *   dt               time step; <= 0 selects cfl_factor * 2 / sqrt(rho_Gershgorin(M^-1 K))
- *                    (Eq. spectral, Section 3.3), recomputed by fwi_set_velocity.
+ *                    (Eq. spectral, Section 3.4), recomputed by fwi_set_velocity.
  *   cfl_factor       fraction of the Gershgorin bound (the paper uses 10-20 % below it).
  *   nsteps           Nt: records hold Nt + 1 samples (t_n = n dt, n = 0..Nt).
  *   box_lo, box_hi   the physical domain Omega_0 (first dim entries used).
@@ -68,7 +68,7 @@ typedef struct fwi_batch fwi_batch;
  *   layout           0: chunked (elements grouped in chunks that assemble in shared memory;
  *                    the default), 1: plain (one thread per element and shot scattering
  *                    with global atomics; the unfused reference form).
- *   tensor_cores     chunked layout, triangles only: in the adjoint steps (Section 3.4,
+ *   tensor_cores     chunked layout, triangles only: in the adjoint steps (Section 3.5,
  *                    with the gradient integrand) the per-element derivative contractions
  *                    (Section 3.2) of a chunk run as tf32 tensor-core MMAs with a three-term
  *                    hi/lo split (near-FP32 products, FP32 accumulation in tensor memory).
@@ -78,6 +78,11 @@ typedef struct fwi_batch fwi_batch;
  *                    record length past 1e-5; in the adjoint it only enters the gradient
  *                    (about 3e-6 against a 1e-4 bound). 0 or -1: off, 1: on (FWI_EINVAL for
  *                    tetrahedra or the plain layout).
+ *   grad_stride      r: subsampling of the gradient's time sum (Section 3.6). Only the time
+ *                    levels n = 0 (mod r) enter Eq. (gradient3), each with weight r, and the
+ *                    adjoint keeps only those forward wavefields (a recompute ring of
+ *                    ckpt_stride / r instead of ckpt_stride). <= 1: every level (the exact
+ *                    discrete gradient). ckpt_stride must be a multiple of r (FWI_EINVAL).
  */
 typedef struct {
   int dim;
@@ -95,6 +100,7 @@ typedef struct {
   double water_speed;
   int layout;
   int tensor_cores;
+  int grad_stride;
 } fwi_params;
 
 /* Builds the DoF numbering, locality order and per-element geometry of a simplex mesh
@@ -135,7 +141,7 @@ int fwi_reference_element(int dim, int k, int* n, double* xhat, double* w, doubl
 
 /* Point location (host only; works on host-only meshes): for each of npts points pts[p][dim]
  * the containing element in the library's element order and the point's reference
- * coordinates xhat[p][dim] (Section 4.3: sources and receivers are evaluated through the
+ * coordinates xhat[p][dim] (Section 4.2: sources and receivers are evaluated through the
  * basis of the element that holds them). Ties (a point on a shared edge or vertex) go to
  * the lowest element of the caller's cell order whose barycentric coordinates are all >=
  * -1e-12. A point in no element gives FWI_EINVAL. elem_out or xhat_out may be NULL. */
@@ -159,7 +165,7 @@ int fwi_set_velocity(fwi_mesh* m, const double* c);
 /* The time step in use. */
 int fwi_get_dt(const fwi_mesh* m, double* dt);
 
-/* A batch of S shots sharing the mesh and a receiver spread (Section 4.3: the source is
+/* A batch of S shots sharing the mesh and a receiver spread (Section 4.2: the source is
  * the transpose of receiver interpolation, b_{g(e,k)} = w(t) phi_k(x_s)).
  * src[S][dim], rec[R][dim] host doubles; every point must lie in the mesh (FWI_EINVAL).
  * Allocates the batch's device state: wavefields, damping-layer auxiliaries, forward
@@ -211,7 +217,7 @@ int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* s
  *     before it returns. */
 int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
 
-/* Discrete adjoint solve (Section 3.4, the transposed recurrence run backwards) driven by
+/* Discrete adjoint solve (Section 3.5, the transposed recurrence run backwards) driven by
  * residual[S][Nt+1][R] = d - dtilde, with the forward wavefield recomputed segment by
  * segment from the checkpoints of the last fwi_forward_shot. Accumulates the integrand of
  * Eq. (gradient3), sum_n 2 c grad u^dagger . grad u, summed over the batch's shots, into
@@ -241,6 +247,14 @@ int fwi_profile_read(fwi_batch* b, double* ms, int64_t* steps);
  * derivative of Eq. control_deriv), masked like fwi_gradient. dJdc_out[N] doubles (host or
  * device), misfit_out may be NULL. Clears the accumulators. */
 int fwi_gradient_raw(fwi_batch* b, double* dJdc_out, double* misfit_out, void* stream);
+
+/* Testing aid (no counterpart in the paper): the number of polls each bounded mbarrier wait
+ * of the tensor-core kernel makes before it gives up (default 2^22; < 0 restores it; 0 gives
+ * up at once). A wait that gives up stops its kernel early, waits (with the default limit)
+ * for its MMAs in flight, frees its tensor memory and sets a status bit; the call then
+ * returns FWI_ETIMEDOUT and the context stays usable. The batch's results of that call are
+ * meaningless. */
+int fwi_batch_set_wait_limit(fwi_batch* b, int polls);
 
 int fwi_batch_free(fwi_batch* b);
 int fwi_mesh_free(fwi_mesh* m);

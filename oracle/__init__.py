@@ -3,7 +3,7 @@
 This package is TEST INFRASTRUCTURE. It is a plain, slow, FP64 restatement of what the
 paper's method computes: KMV reference elements, global lumped mass, stiffness and damping
 layer operators, the leapfrog time step of Eq. (forward3), the discrete adjoint (the
-transposed recurrence of Section 3.4), and the mesh-independent gradient of Eq.
+transposed recurrence of Section 3.5), and the mesh-independent gradient of Eq.
 (gradient3). Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import it. The product path (the CUDA
 library and its Python binding) never imports, calls or links anything here, and this

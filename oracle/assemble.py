@@ -18,7 +18,7 @@ J_e^{-T} Dhat[:, q, j].
            gradient tested against phi_i. D_{u,2} = diag(Psi2_kk c^2) G_k and
            D_{omega,3} = diag(Psi3_kk c^2) G_k (Eq. acoustic_pml_II carries the c^2 that
            Appendix A omits). G_k = D_k^T exactly.
-  H        H_rj = phi_j(x_r) in the element containing x_r (Section 4.3); the source
+  H        H_rj = phi_j(x_r) in the element containing x_r (Section 4.2); the source
            vector of a point source is the same row (its transpose).
 """
 import numpy as np
@@ -87,7 +87,7 @@ def div_and_grad(mesh, chunk=20000):
 
 
 def point_matrix(mesh, points):
-    """Rows phi_j(x_r) for each point (Section 4.3), as a sparse (npoints, N) matrix."""
+    """Rows phi_j(x_r) for each point (Section 4.2), as a sparse (npoints, N) matrix."""
     e, xh = mesh.locate(points)
     phi = mesh.elem.basis(xh)  # (m, n)
     n = mesh.elem.n

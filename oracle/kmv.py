@@ -1,6 +1,6 @@
 """KMV mass-lumped reference elements, FP64 (oracle; test infrastructure only).
 
-What this computes (Section 3.2, "Higher-order mass lumping", and Section 4.2): for a
+What this computes (Section 3.2, "Higher-order mass lumping", and Section 4.1): for a
 degree-k Kong-Mulder-Veldhuizen (KMV) element the finite element space is P_k enriched by
 bubble functions, the nodes of the nodal basis are also the points of a quadrature rule,
 and integrating the mass matrix with that rule makes it diagonal.

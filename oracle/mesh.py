@@ -8,7 +8,7 @@
     on every edge and face, so the positions of a shared node agree between neighbours up
     to rounding. This is checked against the topological count
     V + E_edges*(edge nodes) + F*(face nodes) + T*(interior nodes).
-  * Point location (Section 4.3): the containing element is the lowest-numbered element
+  * Point location (Section 4.2): the containing element is the lowest-numbered element
     whose barycentric coordinates at the point are all >= -1e-12.
 """
 import numpy as np

@@ -1,13 +1,13 @@
 """Leapfrog forward solve, discrete adjoint and gradient, FP64 (oracle; test
 infrastructure only).
 
-State Q^n = [U^n, P^n, Y^n] (Section 3.3): U the pressure, P the auxiliary vector (one
+State Q^n = [U^n, P^n, Y^n] (Section 3.4): U the pressure, P the auxiliary vector (one
 block per direction) and Y = omega (3D only); P and Y exist only when a damping layer is
 present. The recurrence is Eq. (forward3):
 
     A_{n+1} Q^{n+1} + A_n Q^n + A_{n-1} Q^{n-1} = F^n,     F^n = [b^n, 0, 0]
 
-with b^n_i = w(t_n) phi_i(x_s) for a point source (Section 4.3), Q^0 = Q^{-1} = 0, and
+with b^n_i = w(t_n) phi_i(x_s) for a point source (Section 4.2), Q^0 = Q^{-1} = 0, and
 records d^n = H U^n for n = 0..Nt.
 
 Readings of the printed block matrices (garbled in the paper: Delta^{-2} and
@@ -29,7 +29,7 @@ unstable):
   sigma_l (from the complex coordinate stretch that yields Eqs. acoustic_pml-III with the
   paper's signs).
 
-Adjoint (Section 3.4): with the Lagrangian L = J + sum_n Lam^n . R^n the multipliers obey
+Adjoint (Section 3.5): with the Lagrangian L = J + sum_n Lam^n . R^n the multipliers obey
 the transposed recurrence run backwards,
 
     A_{n+1}^T Lam^{m-1} = -dJ/dQ^m - A_n^T Lam^m - A_{n-1}^T Lam^{m+1},   Lam^{Nt} = 0,
@@ -41,7 +41,7 @@ decides for this one.
 
 Gradient, Eq. (gradient3): M G = sum_n int 2 c grad u^dagger(t_n) . grad u(t_n) delta c,
 evaluated with the KMV rule (c and the integrand sampled at the nodes), no dt factor
-(Section 3.4). Away from the boundary and the damping layer this is the exact derivative of
+(Section 3.5). Away from the boundary and the damping layer this is the exact derivative of
 the discrete J; the layer and boundary terms are masked (Section 5.1).
 """
 import numpy as np
@@ -133,10 +133,14 @@ class Operators:
                 hist[n + 1] = Q[:N]
         return rec, hist
 
-    def adjoint(self, H, residual, U_hist=None):
+    def adjoint(self, H, residual, U_hist=None, r=1, offset=0):
         """Backward transposed recurrence. residual = d - dtilde, (nt+1, R).
         Returns (Lam_u history (nt+1, N), gradient sum g (N,) or None). g_i is
-        sum_n 2 c_i sum_{e ∋ i} w_i |J_e| grad u^dagger^n(x_i) . grad U^n(x_i)."""
+        sum_n 2 c_i sum_{e ∋ i} w_i |J_e| grad u^dagger^n(x_i) . grad U^n(x_i).
+
+        Subsampling (Section 3.6): with r > 1 only the time levels n = offset (mod r) enter
+        the sum, each with weight r (the rectangle rule on a time grid r times coarser), so
+        that only every r-th forward wavefield is needed."""
         N = self.mesh.N
         nt = residual.shape[0] - 1
         L_next = np.zeros(self.nblk * N)   # Lam^{m+1}
@@ -152,8 +156,8 @@ class Operators:
             L_prev = (rhs - A0T @ L - self.A_minus * L_next) / self.A_plus
             L_next, L = L, L_prev
             hist[m - 1] = L[:N]
-            if g is not None:
-                g += self._integrand(GR, L[:N], U_hist[m - 1])
+            if g is not None and (m - 1 - offset) % r == 0:
+                g += r * self._integrand(GR, L[:N], U_hist[m - 1])
         return hist, g
 
     # -- gradient (Eq. gradient3) -------------------------------------------------------
@@ -198,13 +202,13 @@ class Operators:
 
 def misfit(rec, rec_obs):
     """J = 1/2 sum_n sum_r (d - dtilde)^2, plain sums with no dt (Eq. l2error read as in
-    Section 3.4)."""
+    Section 3.5)."""
     r = rec - rec_obs
     return 0.5 * float(np.sum(r * r))
 
 
 def point_source_rhs(mesh, x_s, wavelet):
-    """b^n = w(t_n) phi(x_s) (Section 4.3)."""
+    """b^n = w(t_n) phi(x_s) (Section 4.2)."""
     b = np.asarray(assemble.point_matrix(mesh, np.atleast_2d(x_s)).todense()).ravel()
     wav = np.asarray(wavelet, dtype=np.float64)
     return lambda n: wav[n] * b

@@ -160,6 +160,7 @@ struct fwi_mesh {
 struct fwi_batch {
   fwi_mesh* m = nullptr;
   int S = 0, log2S = 0, R = 0, nt = 0, K = 0, C = 0;
+  int gstride = 1;  // gradient subsampling stride r (Section 3.6); the ring holds K / r fields
   std::vector<int32_t> src_elem;   // [S] new element index
   std::vector<float> src_phi;      // [S][nn]
   std::vector<int32_t> rec_elem;   // [R]
@@ -193,6 +194,7 @@ struct fwi_batch {
   double* stage_grad = nullptr;
   bool forward_done = false;
   int launch_error = 0;  // first kernel configuration error of a call (cudaError_t)
+  int tc_wait_limit = 1 << 22;  // polls of each bounded wait of the tensor-core kernel
   // optional per-kernel timing with CUDA events (fwi_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -518,6 +520,9 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
   std::unique_ptr<fwi_mesh> m(new fwi_mesh());
   m->p = *params;
   if (m->p.ckpt_stride <= 0) m->p.ckpt_stride = 50;
+  if (m->p.grad_stride <= 1) m->p.grad_stride = 1;
+  if (m->p.ckpt_stride % m->p.grad_stride != 0)
+    return fail(FWI_EINVAL, "ckpt_stride must be a multiple of grad_stride");
   if (m->p.cfl_factor <= 0) m->p.cfl_factor = 0.9;
   m->dim = d;
   m->k = params->k;
@@ -677,11 +682,17 @@ int mesh_create(const double* verts, int64_t nverts, const int32_t* cells, int64
     }
     m->ch_own_lo[nch] = cur;
     m->N_own = cur;
-    for (int e = 0; e < E; ++e)
-      for (int q = 0; q < m->ns; ++q) {
-        int pid = m->conn[(size_t)e * n + q];
-        if (fin[pid] < 0) fin[pid] = cur++;
-      }
+    // halo DoFs: those no damping-layer element touches first, then the layer DoFs, so that
+    // the node kernel's warps see one kind of DoF
+    std::vector<char> in_layer(nprov, 0);
+    for (int e = m->E0; e < E; ++e)
+      for (int q = 0; q < m->ns; ++q) in_layer[m->conn[(size_t)e * n + q]] = 1;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int e = 0; e < E; ++e)
+        for (int q = 0; q < m->ns; ++q) {
+          int pid = m->conn[(size_t)e * n + q];
+          if (fin[pid] < 0 && in_layer[pid] == pass) fin[pid] = cur++;
+        }
     m->N = cur;
     m->Ns = nprov;  // number of shared DoFs (owned + halo)
     for (int e = 0; e < E; ++e)
@@ -1081,6 +1092,7 @@ int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const
   b->R = nrec;
   b->nt = m->p.nsteps;
   b->K = m->p.ckpt_stride;
+  b->gstride = m->p.grad_stride;
   b->C = (b->nt + b->K - 1) / b->K;
   if (b->nt <= 0) return fail(FWI_EINVAL, "nsteps must be positive");
   const int d = m->dim, n = m->nn, N = m->N, S = b->S;
@@ -1127,7 +1139,7 @@ int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const
       (rc = dalloc(&b->Y, YS)) || (rc = dalloc(&b->Yacc, YS)) || (rc = dalloc(&b->ua, NS_)) ||
       (rc = dalloc(&b->va, NS_)) || (rc = dalloc(&b->Pa, LS)) || (rc = dalloc(&b->Ya, YS)) ||
       (rc = dalloc(&b->ckpt, b->state_floats() * b->C)) ||
-      (rc = dalloc(&b->ring, NS_ * b->K)) || (rc = dalloc(&b->gseg, (size_t)N)) ||
+      (rc = dalloc(&b->ring, NS_ * (b->K / b->gstride))) || (rc = dalloc(&b->gseg, (size_t)N)) ||
       (rc = dalloc(&b->gsum, (size_t)N)) || (rc = dalloc(&b->gcomp, (size_t)N)) ||
       (rc = dalloc(&b->misfit, 1)) || (rc = dalloc(&b->status, 1)))
     return rc;
@@ -1210,6 +1222,7 @@ StepArgs base_args(fwi_batch* b) {
   a.R = b->R;
   a.gseg = b->gseg;
   a.status = b->status;
+  a.tc_wait_limit = b->tc_wait_limit;
   return a;
 }
 
@@ -1409,18 +1422,22 @@ int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
     float *cu, *cv, *cP, *cY;
     ckpt_ptrs(b, c, &cu, &cv, &cP, &cY);
     if (int rc = copy_state(b, b->u, b->v, b->P, b->Y, cu, cv, cP, cY, st)) return rc;
+    // the ring keeps U^n for the levels n = 0 (mod r) of the segment (n0 is one of them)
+    const int r = b->gstride;
     CUDA_TRY(cudaMemcpyAsync(b->ring, b->u, NS_ * sizeof(float), cudaMemcpyDeviceToDevice, st));
     for (int n = n0; n < n1 - 1; ++n) {
       forward_steps(b, n, n + 1, b->wav_dev, nullptr, false, st);
-      CUDA_TRY(cudaMemcpyAsync(b->ring + NS_ * (size_t)(n + 1 - n0), b->u, NS_ * sizeof(float),
-                               cudaMemcpyDeviceToDevice, st));
+      if ((n + 1) % r == 0)
+        CUDA_TRY(cudaMemcpyAsync(b->ring + NS_ * (size_t)((n + 1 - n0) / r), b->u,
+                                 NS_ * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     for (int mm = n1 - 1; mm >= std::max(n0, 1); --mm) {
       a.n = mm;
-      a.ring_u = b->ring + NS_ * (size_t)(mm - n0);
+      // the gradient integrand at the subsampled levels only (the others: adjoint step alone)
+      a.ring_u = mm % r == 0 ? b->ring + NS_ * (size_t)((mm - n0) / r) : nullptr;
       run_step(b, a, st);
     }
-    fwi::launch_fold(b->gseg, b->gsum, b->gcomp, b->m->N, st);
+    fwi::launch_fold(b->gseg, b->gsum, b->gcomp, b->m->N, (double)r, st);
     g_launches += 1;
   }
   return check_status(b, st);
@@ -1601,7 +1618,8 @@ int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes) {
   f += 3 * Nl * d * S + 2 * Nl * S;     // P, Pacc, PaccY, Y, Yacc
   f += 2 * N * S + Nl * d * S + Nl * S; // adjoint state
   f += state * C;                       // checkpoints
-  f += N * S * K;                       // recompute ring
+  const int64_t r = m->p.grad_stride > 1 ? m->p.grad_stride : 1;
+  f += N * S * (K / r);                 // recompute ring (subsampled levels only)
   f += N;                               // FP32 gradient segment
   f += 2 * S * (nt + 1) * nrec + S * nt;  // records, residual, wavelet copies
   *bytes = f * 4 + 2 * N * 8 + (int64_t)m->E * 4;
@@ -1630,6 +1648,12 @@ int fwi_gradient_raw(fwi_batch* b, double* dJdc_out, double* misfit_out, void* s
   CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, (size_t)N * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(b->misfit, 0, sizeof(double), st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int fwi_batch_set_wait_limit(fwi_batch* b, int polls) {
+  if (!b) return fail(FWI_EINVAL, "null batch");
+  b->tc_wait_limit = polls < 0 ? (1 << 22) : polls;
   return 0;
 }
 

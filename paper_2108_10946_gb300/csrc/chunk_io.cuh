@@ -9,10 +9,9 @@
 // behind the element phase. Phase 3 (chunk_store) finishes the owned DoFs from the table
 // and sends the halo DoFs' contributions to the global accumulators.
 //
-// Layer chunks of steps without the gradient add a third group (chunk_load_layer, issued
-// once the layer indices are in the table): the damping-layer auxiliaries P (and in the 3D
-// forward Y) of every local layer DoF. Gradient steps, whose table is the largest, read P
-// from global memory instead, so that two CTAs still fit on an SM.
+// Layer chunks add a third group (chunk_load_layer, issued once the layer indices are in the
+// table): the damping-layer auxiliaries P (and in the 3D forward Y) of every local layer DoF;
+// the element phase and the update read them from the table.
 //
 // Layer chunks (two to four times the table of the others) skip group 1 and read v and
 // c1..c3 from global memory in phase 3, which keeps two of their CTAs on an SM.
@@ -20,8 +19,8 @@
 // Table layout (floats, shot-major [SG][Lm] with Lm odd so that the SG rows of one DoF fall
 // in different banks): u, y [SG][Lm]; c2 [Lm]; pi [Lm] (int); v [SG][Lm] and cf [3][Lm]
 // (not in layer chunks); gradient
-// steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm], P [D][SG][Lm] (not in
-// gradient steps) (and in 3D sY [D][SG][Lm], yw [SG][Lm], Yv [SG][Lm]).
+// steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm], P [D][SG][Lm] (and in 3D
+// sY [D][SG][Lm], yw [SG][Lm], Yv [SG][Lm]).
 #pragma once
 #include "update.cuh"
 
@@ -47,7 +46,7 @@ __host__ __device__ inline size_t chunk_tab_floats(int L, int SG, int D, bool gr
   const size_t Lm = (size_t)chunk_stride(L);
   size_t f = Lm * (2 * (size_t)SG + 2) + (layer ? 0 : Lm * ((size_t)SG + 3));
   if (grad) f += Lm * ((size_t)SG + 2);
-  if (layer) f += (grad ? 1 : 2) * Lm * D * SG + (D == 3 ? Lm * D * SG + 2 * Lm * SG : 0);
+  if (layer) f += 2 * Lm * D * SG + (D == 3 ? Lm * D * SG + 2 * Lm * SG : 0);
   return f;
 }
 
@@ -74,7 +73,7 @@ __device__ __forceinline__ ChunkTab chunk_tab(float* base, int Lm, int SG, int D
   p = t.cv + (grad ? Lm : 0);
   t.s = p;
   t.P = t.s + (layer ? (size_t)D * R : 0);
-  t.sY = t.P + (layer && !grad ? (size_t)D * R : 0);
+  t.sY = t.P + (layer ? (size_t)D * R : 0);
   t.yw = t.sY + (layer && D == 3 ? (size_t)D * R : 0);
   t.Yv = t.yw + (layer && D == 3 ? R : 0);
   return t;
@@ -178,6 +177,27 @@ __device__ __forceinline__ void chunk_load_layer(const StepArgs& a, const ChunkD
   cp_async_commit();
 }
 
+// Layer chunks, at the start of the element phase: the update phase reads v, c1..c3 and the
+// layer coefficients of the owned DoFs from global memory; start bringing them to L2 so that
+// those reads do not each wait for DRAM.
+template <int D>
+__device__ __forceinline__ void chunk_prefetch_update(const StepArgs& a, const ChunkDesc& cd,
+                                                      const ChunkTab& t, int SG, int s0, int tid,
+                                                      int nth) {
+  typedef LayerCoef<D> LC;
+  for (int l = tid; l < cd.own_n; l += nth) {
+    const size_t dof = (size_t)(cd.own_lo + l);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.v + dof * a.S + s0));
+    if ((l & 31) == 0) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.cf + (size_t)r * a.N + dof));
+    }
+    const int pi = t.pi[l];
+    if (pi >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.lcf + (size_t)pi * LC::COUNT));
+  }
+  (void)SG;
+}
+
 // Phase 3: owned DoFs final (the increment update from the table), halo DoFs to the
 // global accumulators (finished by the node kernel after all chunks), gradient segment.
 // Call after cp_async_wait<0>() and a barrier.
@@ -215,11 +235,11 @@ __device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& 
           sU[d] = t.s[(size_t)(d * SG + q) * Lm + l];
           sY[d] = 0.f;
           if constexpr (D == 3) sY[d] = t.sY[(size_t)(d * SG + q) * Lm + l];
-          po[d] = GRAD ? 0.f : t.P[(size_t)(d * SG + q) * Lm + l];
+          po[d] = t.P[(size_t)(d * SG + q) * Lm + l];
         }
         if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
         dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], vo[k], c1[k], c2[k],
-                          c3[k], t.pi[l], sU, sY, ywv, GRAD ? nullptr : po);
+                          c3[k], t.pi[l], sU, sY, ywv, po);
       }
     }
   } else {

@@ -21,16 +21,9 @@
 namespace fwi {
 
 // d = a * b + c on two FP32 lanes at once (packed FP32x2 FMA of the sm_100 family; each
-// lane an IEEE fused multiply-add rounded to nearest)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;"
-      : "=l"(r)
-      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
-        "l"(*reinterpret_cast<unsigned long long*>(&b)),
-        "l"(*reinterpret_cast<unsigned long long*>(&c)));
-  return *reinterpret_cast<float2*>(&r);
-}
+// lane an IEEE fused multiply-add rounded to nearest). The compiler intrinsic lets the
+// register allocator keep the operands in aligned pairs.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
 // (plus, for the rolled per-node loop, the per-thread local connectivity and, for triangles
@@ -98,8 +91,9 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   }
   cp_async_wait<1>();
   __syncthreads();
-  if (layer && !grad) {
+  if (layer) {
     chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+    chunk_prefetch_update<D>(a, cd, t, SG, s0, tid, nth);
     cp_async_wait<0>();
     __syncthreads();
   }
@@ -230,7 +224,7 @@ if constexpr (ROLL) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -248,7 +242,7 @@ if constexpr (ROLL) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
+                pw[k] = t.P[(size_t)(k * SG + sl) * Lm + lqq] *
                         __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)
@@ -355,7 +349,7 @@ if constexpr (ROLL) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -373,7 +367,7 @@ if constexpr (ROLL) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
+                pw[k] = t.P[(size_t)(k * SG + sl) * Lm + lqq] *
                         __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)
@@ -473,7 +467,7 @@ if constexpr (ROLL) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -491,7 +485,7 @@ if constexpr (ROLL) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
+                pw[k] = t.P[(size_t)(k * SG + sl) * Lm + lqq] *
                         __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)

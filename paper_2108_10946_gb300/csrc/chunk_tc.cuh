@@ -194,8 +194,9 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
     }
     cp_async_wait<1>();  // the element phase's group
     __syncthreads();
-    if (layer && !grad) {
+    if (layer) {
       chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+      chunk_prefetch_update<D>(a, cd, t, SG, s0, tid, nth);
       cp_async_wait<0>();
       __syncthreads();
     }
@@ -239,7 +240,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
       tc::mma_commit(&bar);
     }
     {
-      const bool ok = tc::mbar_wait(&bar, parity, kTcWaitLimit);
+      const bool ok = tc::mbar_wait(&bar, parity, a.tc_wait_limit);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -280,7 +281,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
                 sq[k] = wq * (Am[0 * 2 + k] * g0 + Am[1 * 2 + k] * g1);
-                const float raw = grad ? a.P[((size_t)pi * 2 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
+                const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
                 pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
               }
               f0 += wq * (Am[0] * pq[0] + Am[1] * pq[1]);
@@ -326,7 +327,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
       tc::mma_commit(&bar);
     }
     {
-      const bool ok = tc::mbar_wait(&bar, parity, kTcWaitLimit);
+      const bool ok = tc::mbar_wait(&bar, parity, a.tc_wait_limit);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -388,8 +389,9 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
   }
 
   if (failed) {
-    // a wait gave up: report it, give the tensor cores one more bounded wait for the
-    // MMAs still in flight, then free the tensor memory
+    // a wait gave up: report it, give the tensor cores one more bounded wait (the full
+    // default limit, whatever the batch's setting) for the MMAs still in flight, then free the
+    // tensor memory
     if (tid == 0) atomicOr(a.status, 2);
     tc::mbar_wait(&bar, parity, kTcWaitLimit);
   }

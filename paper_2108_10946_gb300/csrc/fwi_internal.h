@@ -32,6 +32,7 @@ struct StepArgs {
   const int* halo;           // halo DoF ids, chunk by chunk
   const unsigned short* lconn;  // [NS][Es] chunk-local index of each shared node
   int tc;              // chunked layout, 2D: element contraction on the tensor cores
+  int tc_wait_limit;   // polls of each bounded mbarrier wait of the tensor-core kernel
   int mode;            // 0 forward, 1 adjoint (with gradient when ring != null)
   int n;               // time index (forward: step n -> n+1; adjoint: step m)
   int nt;
@@ -94,7 +95,8 @@ const KernelSet* kernel_set(int dim, int k);
 
 // Generic (dimension-only) kernels.
 void launch_node_update(const StepArgs& a, int dim, cudaStream_t st);
-void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, cudaStream_t st);
+void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, double scale,
+                 cudaStream_t st);
 void launch_finish_gradient(const double* gsum, const double* gcomp, const float* Minv_unused,
                             const double* M, const unsigned char* mask, double* out, int64_t N,
                             cudaStream_t st);

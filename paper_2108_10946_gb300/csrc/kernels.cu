@@ -28,6 +28,16 @@ const KernelSet* kernel_set(int dim, int k) {
 
 void launch_node_update(const StepArgs& a, int dim, cudaStream_t st) {
   const int bs = 256;
+  if (a.S % 4 == 0) {  // one thread per (DoF, four shots)
+    const int64_t items4 = (int64_t)a.hcnt * (a.S / 4);
+    if (items4 == 0) return;
+    const unsigned blocks4 = (unsigned)((items4 + bs - 1) / bs);
+    if (dim == 2)
+      node_kernel4<2><<<blocks4, bs, 0, st>>>(a);
+    else
+      node_kernel4<3><<<blocks4, bs, 0, st>>>(a);
+    return;
+  }
   const int64_t items = (int64_t)a.hcnt * a.S;
   if (items == 0) return;
   const unsigned blocks = (unsigned)((items + (int64_t)bs * NODE_ITEMS - 1) / ((int64_t)bs * NODE_ITEMS));
@@ -40,10 +50,10 @@ void launch_node_update(const StepArgs& a, int dim, cudaStream_t st) {
 // Kahan fold of the FP32 segment sum into (sum, comp); comp carries the lost low part
 // with the sign convention sum - comp ~ exact.
 __global__ void fold_kernel(float* __restrict__ gseg, double* __restrict__ gsum,
-                            double* __restrict__ gcomp, int64_t N) {
+                            double* __restrict__ gcomp, int64_t N, double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double x = (double)gseg[i];
+  const double x = scale * (double)gseg[i];  // scale: the subsampling weight r
   gseg[i] = 0.f;
   const double s = gsum[i];
   const double y = x - gcomp[i];
@@ -52,9 +62,10 @@ __global__ void fold_kernel(float* __restrict__ gseg, double* __restrict__ gsum,
   gsum[i] = t;
 }
 
-void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, cudaStream_t st) {
+void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, double scale,
+                 cudaStream_t st) {
   if (N == 0) return;
-  fold_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gseg, gsum, gcomp, N);
+  fold_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gseg, gsum, gcomp, N, scale);
 }
 
 __global__ void finish_kernel(const double* __restrict__ gsum, const double* __restrict__ gcomp,

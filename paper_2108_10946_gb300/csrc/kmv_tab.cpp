@@ -398,11 +398,14 @@ bool solve_orbits(const std::string& kinds, const std::vector<ld>& fixed,
 
 namespace {
 // Solves the small dense system M z = r (M square, order m) by Gaussian elimination with
-// partial pivoting in long double; a tiny ridge keeps a rank-deficient M solvable.
+// partial pivoting in long double. A pivot below 1e-13 of the largest diagonal entry counts
+// as zero and its unknown is set to 0 (a truncated solve): a rank-deficient M must give a
+// bounded z whatever the width of long double (80-bit on x86, 128-bit on Arm).
 void dense_solve(std::vector<ld> M, std::vector<ld> r, int m, std::vector<ld>& z) {
-  ld tr = 0;
-  for (int i = 0; i < m; ++i) tr += std::fabs(M[i * m + i]);
-  for (int i = 0; i < m; ++i) M[i * m + i] += 1e-28L * (tr + 1e-300L);
+  ld scale = 0;
+  for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(M[i * m + i]));
+  const ld tiny = 1e-13L * scale;
+  std::vector<char> dead(m, 0);
   for (int c = 0; c < m; ++c) {
     int p = c;
     for (int i = c + 1; i < m; ++i)
@@ -412,7 +415,10 @@ void dense_solve(std::vector<ld> M, std::vector<ld> r, int m, std::vector<ld>& z
       std::swap(r[c], r[p]);
     }
     const ld d = M[c * m + c];
-    if (d == 0) continue;
+    if (!(std::fabs(d) > tiny)) {
+      dead[c] = 1;
+      continue;
+    }
     for (int i = c + 1; i < m; ++i) {
       const ld f = M[i * m + c] / d;
       if (f == 0) continue;
@@ -422,9 +428,10 @@ void dense_solve(std::vector<ld> M, std::vector<ld> r, int m, std::vector<ld>& z
   }
   z.assign(m, 0);
   for (int i = m - 1; i >= 0; --i) {
+    if (dead[i]) continue;
     ld s = r[i];
     for (int j = i + 1; j < m; ++j) s -= M[i * m + j] * z[j];
-    z[i] = M[i * m + i] != 0 ? s / M[i * m + i] : 0;
+    z[i] = s / M[i * m + i];
   }
 }
 
@@ -494,7 +501,16 @@ void round_keeping(const std::vector<ld>& x0, const std::vector<ld>& A, const st
     val[j] = (ld)(float)x[j];
     fixed[j] = 1;
   }
-  for (int j = 0; j < n; ++j) out[j] = (float)val[j];
+  // never trade accuracy of the entries for the identities: a row whose entries would move by
+  // more than four spacings of its largest entry is rounded to nearest instead
+  ld big = 0;
+  for (int j = 0; j < n; ++j) big = std::max(big, std::fabs(x0[j]));
+  const float fb = (float)big;
+  const ld spb = (ld)std::nextafter(fb, INFINITY) - (ld)fb;
+  bool ok = true;
+  for (int j = 0; j < n; ++j)
+    if (!std::isfinite((double)val[j]) || std::fabs(val[j] - x0[j]) > 4 * spb) ok = false;
+  for (int j = 0; j < n; ++j) out[j] = ok ? (float)val[j] : (float)x0[j];
 }
 
 ld mono_at(const int* e, const double* x, int dim) {

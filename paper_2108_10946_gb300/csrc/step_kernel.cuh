@@ -7,7 +7,7 @@
 //              f_q = w_q c_q^2 Ghat ghat_q + w_q A P_q            (K U + D P)
 //            ghat_q = sum_j Dhat[q][j] U_j, Ghat = |J| J^-1 J^-T, A = |J| J^-1;
 //            layer scatter s_q = w_q A^T ghat_q                    (lumped G U of D_{u,2})
-//   adjoint  (Section 3.4, transposed recurrence): the same with U -> lam and
+//   adjoint  (Section 3.5, transposed recurrence): the same with U -> lam and
 //            P -> Psi2 c^2 nu (Q^T nu), s_q giving D^T lam; with the forward field U^m of
 //            the recompute ring it also forms the integrand of Eq. (gradient3),
 //              2 c_q w_q (ghat lam_q)^T Ghat (ghat U_q).

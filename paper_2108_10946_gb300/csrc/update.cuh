@@ -199,4 +199,108 @@ __global__ void __launch_bounds__(256) node_kernel(const StepArgs a) {
   }
 }
 
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ldcg4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float comp(const float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+__device__ __forceinline__ void setc(float4& v, int c, float x) {
+  if (c == 0) v.x = x; else if (c == 1) v.y = x; else if (c == 2) v.z = x; else v.w = x;
+}
+
+// The shared-DoF finish of node_kernel for batches of S = 4m shots: one thread per (DoF,
+// four consecutive shots), float4 reads and writes of the shot-interleaved arrays, the same
+// arithmetic as dof_update_pre on each shot. A layer DoF issues all of its layer reads (the
+// accumulated layer sums, the auxiliaries and their coefficients) at once, after its layer
+// index; the halo numbers the layer DoFs last, so warps stay uniform.
+template <int D>
+__global__ void __launch_bounds__(256) node_kernel4(const StepArgs a) {
+  typedef LayerCoef<D> L;
+  const int S = a.S, ngrp = S >> 2;
+  const int64_t total = (int64_t)a.hcnt * ngrp;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t i = t / ngrp;
+  const int s0 = (int)(t - i * ngrp) * 4;
+  const int dof = a.h0 + (int)i;
+  const size_t ix = (size_t)dof * S + s0, rx = (size_t)i * S + s0;
+  const float4 uo = ld4(a.u + ix), vo = ld4(a.v + ix), y = ldcg4(a.r + rx);
+  const float c1 = __ldg(a.cf + dof), c2 = __ldg(a.cf + (size_t)a.N + dof);
+  const float c3 = __ldg(a.cf + 2 * (size_t)a.N + dof);
+  const int pi = __ldg(a.pidx + dof);
+  st4(a.r + rx, make_float4(0.f, 0.f, 0.f, 0.f));
+  float4 vn;
+  vn.x = c1 * vo.x - c2 * y.x - c3 * uo.x;
+  vn.y = c1 * vo.y - c2 * y.y - c3 * uo.y;
+  vn.z = c1 * vo.z - c2 * y.z - c3 * uo.z;
+  vn.w = c1 * vo.w - c2 * y.w - c3 * uo.w;
+  if (pi >= 0) {
+    const float* lc = a.lcf + (size_t)pi * L::COUNT;
+    float4 sU[D], sY[D], Po[D];
+    float e1[D], e2[D], e3[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const size_t pk = ((size_t)pi * D + k) * S + s0;
+      sU[k] = ldcg4(a.Pacc + pk);
+      Po[k] = ld4(a.P + pk);
+      sY[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (D == 3) {
+        if (a.mode == 0) sY[k] = ldcg4(a.PaccY + pk);
+      }
+      e1[k] = __ldg(lc + L::E1 + k);
+      e2[k] = __ldg(lc + (a.mode == 0 ? L::E2F : L::E2A) + k);
+      e3[k] = D == 3 && a.mode == 0 ? __ldg(lc + L::E3F + k) : 0.f;
+    }
+    float4 Yo = make_float4(0.f, 0.f, 0.f, 0.f), yw = Yo;
+    float cy0 = 0.f, cy1 = 0.f, cy2 = 0.f;
+    const size_t py = (size_t)pi * S + s0;
+    if constexpr (D == 3) {
+      Yo = ld4(a.Y + py);
+      if (a.mode == 1) yw = ldcg4(a.Yacc + py);
+      cy0 = __ldg(lc + (a.mode == 0 ? L::C4 : L::C5));
+      cy1 = __ldg(lc + L::DTDET);
+      cy2 = __ldg(lc + L::DTM);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const size_t pk = ((size_t)pi * D + k) * S + s0;
+      float4 pn;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float x = e1[k] * comp(Po[k], c) - e2[k] * comp(sU[k], c);  // e2: E2F or E2A
+        if (D == 3 && a.mode == 0) x += e3[k] * comp(sY[k], c);
+        setc(pn, c, x);
+      }
+      st4(a.P + pk, pn);
+      st4(a.Pacc + pk, make_float4(0.f, 0.f, 0.f, 0.f));
+      if constexpr (D == 3) {
+        if (a.mode == 0) st4(a.PaccY + pk, make_float4(0.f, 0.f, 0.f, 0.f));
+      }
+    }
+    if constexpr (D == 3) {
+      float4 Yn;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float yo = comp(Yo, c), uc = comp(uo, c);
+        if (a.mode == 0) {
+          setc(vn, c, comp(vn, c) - cy0 * yo);
+          setc(Yn, c, yo + a.dt * uc);
+        } else {
+          setc(vn, c, comp(vn, c) + cy0 * yo);
+          setc(Yn, c, yo - cy1 * uc + cy2 * comp(yw, c));
+        }
+      }
+      st4(a.Y + py, Yn);
+      if (a.mode == 1) st4(a.Yacc + py, make_float4(0.f, 0.f, 0.f, 0.f));
+    }
+  }
+  float4 un;
+  un.x = uo.x + vn.x;
+  un.y = uo.y + vn.y;
+  un.z = uo.z + vn.z;
+  un.w = uo.w + vn.w;
+  st4(a.v + ix, vn);
+  st4(a.u + ix, un);
+  if (!(isfinite(un.x) && isfinite(un.y) && isfinite(un.z) && isfinite(un.w))) atomicOr(a.status, 1);
+}
+
 }  // namespace fwi

@@ -28,7 +28,8 @@ class Params(ctypes.Structure):
                 ("layer_faces", ctypes.c_int), ("layer_width", ctypes.c_double),
                 ("sigma_max", ctypes.c_double), ("absorbing", ctypes.c_int),
                 ("ckpt_stride", ctypes.c_int), ("water_speed", ctypes.c_double),
-                ("layout", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("layout", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("grad_stride", ctypes.c_int)]
 
 
 _lib = None
@@ -73,6 +74,7 @@ def load():
         "fwi_batch_bytes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64)]),
         "fwi_gradient_raw": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+        "fwi_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_profile_read": (ctypes.c_int, [_P, _P, _P]),
         "fwi_mesh_free": (ctypes.c_int, [_P]),
         "fwi_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
@@ -162,7 +164,7 @@ class Mesh:
 
     def __init__(self, verts, cells, k, nsteps, dt=0.0, cfl_factor=0.9, box=None, layer_faces=0,
                  layer_width=0.0, sigma_max=0.0, absorbing=False, ckpt_stride=50, water_speed=0.0,
-                 host_only=False, layout=0, tensor_cores=0):
+                 host_only=False, layout=0, tensor_cores=0, grad_stride=1):
         lib = load()
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -184,6 +186,7 @@ class Mesh:
         p.water_speed = float(water_speed)
         p.layout = int(layout)
         p.tensor_cores = int(tensor_cores)
+        p.grad_stride = int(grad_stride)
         self.params = p
         self.dim = p.dim
         h = ctypes.c_void_p()
@@ -314,6 +317,10 @@ class Batch:
         J = ctypes.c_double()
         _check(_lib.fwi_gradient(self._h, _ptr(out), ctypes.byref(J), _stream_ptr(stream)))
         return J.value
+
+    def set_wait_limit(self, polls):
+        """Polls per bounded tensor-core wait (testing aid; -1 restores the default)."""
+        _check(_lib.fwi_batch_set_wait_limit(self._h, int(polls)))
 
     def profile(self, enable=True):
         _check(_lib.fwi_profile(self._h, int(bool(enable))))

@@ -81,3 +81,45 @@ def test_batch_beyond_device_memory_returns_enomem(pkg):
     dt = probe.dt
     probe.close()
     _healthy_forward(pkg, V, C, 2, dt)
+
+
+def test_tensor_core_wait_that_gives_up_returns_etimedout(pkg):
+    """The tensor-core adjoint kernel's mbarrier waits are bounded. With the batch's limit set
+    to 0 polls every first wait gives up at once: the kernel stops early (after a wait with
+    the full limit for its MMAs in flight and freeing its tensor memory), the call returns
+    FWI_ETIMEDOUT, and with the default limit restored the same batch gives the gradient of a
+    healthy run."""
+    from paper_2108_10946_gb300.lib import FWI_ETIMEDOUT, FwiError
+    V, C = meshes.structured_tri(12, 12)
+    probe = pkg.Mesh(V, C, 4, 1, dt=0.0, cfl_factor=0.8)
+    probe.set_velocity(models.smooth2d(probe.dof_coords()))
+    dt = probe.dt
+    probe.close()
+    nt = 120
+    mesh = pkg.Mesh(V, C, 4, nt, dt=dt, ckpt_stride=20, tensor_cores=1)
+    mesh.set_velocity(models.smooth2d(mesh.dof_coords()))
+    b = pkg.Batch(mesh, np.array([[0.5, 0.3], [0.3, 0.6], [0.6, 0.4], [0.4, 0.2]]),
+                  np.array([[0.4, 0.8], [0.6, 0.8]]))
+    wav = torch.from_numpy(np.stack([signals.ricker_samples(8.0, dt, nt)] * 4)).float().cuda()
+    rec = torch.zeros((4, nt + 1, 2), device="cuda")
+    G0 = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+    b.forward(wav, rec)
+    res = (0.1 * rec).contiguous()
+    b.adjoint(res)
+    b.gradient(G0)
+    b.forward(wav, rec)
+    b.set_wait_limit(0)
+    with pytest.raises(FwiError, match="gave up") as ei:
+        b.adjoint(res)
+    assert ei.value.code == FWI_ETIMEDOUT
+    b.set_wait_limit(-1)
+    G1 = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+    b.gradient(G1)  # clears what the failed call accumulated
+    b.forward(wav, rec)
+    b.adjoint(res)
+    b.gradient(G1)
+    rel = float(torch.linalg.norm(G1 - G0) / torch.linalg.norm(G0))
+    print(f"gradient after the timed-out call against before: rel-L2 {rel:.2e}")
+    assert rel < 1e-5  # the same computation; only the order of the atomic sums differs
+    b.close()
+    mesh.close()

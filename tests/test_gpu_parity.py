@@ -252,3 +252,62 @@ def test_shot_batch_of_four_matches_two_batches_of_two(lib, dim):
     gerr = rel_l2(g4, ga + gb)
     print(f"dim={dim}: gradient rel-L2 = {gerr:.3e}")
     assert gerr < 1e-6
+
+
+@pytest.mark.parametrize("r", [4, 10])
+def test_subsampled_gradient_matches_oracle(lib, r):
+    """Gradient subsampling r (Section 3.6): only the time levels n = 0 (mod r) enter Eq.
+    gradient3, weight r, and the recompute ring holds ckpt_stride / r wavefields. The GPU
+    gradient matches the oracle's subsampled gradient; the printout gives its departure
+    from the full (r = 1) gradient and the ring's memory."""
+    from oracle import assemble
+    k = 3
+    V, C, lay = _case2d(k, n=12, layer=True)
+    cfun = models.smooth2d
+    probe = OracleCase(V, C, k, cfun, 1.0, 1, layer=lay, absorbing=True)
+    dt = 0.8 * probe.ops.cfl_dt()
+    nt = int(round(0.7 / dt))
+    orc = OracleCase(V, C, k, cfun, dt, nt, layer=lay, absorbing=True)
+    srcs = np.array([[0.5, 0.1], [0.2, 0.15], [0.7, 0.2], [0.4, 0.12]])
+    recs = np.array([[x, 0.9] for x in np.linspace(0.05, 0.95, 11)])
+    wav = np.stack([signals.ricker_samples(8.0, dt, nt, t0=0.15) * (1 + 0.1 * i) for i in range(4)])
+    H = assemble.point_matrix(orc.mesh, recs)
+    g_r = np.zeros(orc.mesh.N)
+    g_1 = np.zeros(orc.mesh.N)
+    recs_o = []
+    for s in range(4):
+        rec, U = orc.forward(srcs[s], recs, wav[s].astype(np.float64), store=True)
+        recs_o.append(rec)
+        res = 0.1 * rec.astype(np.float32).astype(np.float64)
+        g_r += orc.ops.adjoint(H, res, U_hist=U, r=r)[1]
+        g_1 += orc.ops.adjoint(H, res, U_hist=U)[1]
+    box = [tuple(b) for b in lay["box"]]
+    out = {}
+    for stride in (1, r):
+        mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=True, ckpt_stride=20, box=box,
+                        layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"],
+                        grad_stride=stride)
+        xg = mesh.dof_coords()
+        mesh.set_velocity(cfun(xg))
+        perm = match_dofs(orc.mesh.coords, xg, 1.0)
+        b = lib.Batch(mesh, srcs, recs)
+        rec = torch.zeros((4, nt + 1, len(recs)), device="cuda")
+        b.forward(torch.from_numpy(wav).float().cuda(), rec)
+        res = torch.from_numpy(np.stack([0.1 * ro for ro in recs_o]).astype(np.float32)).cuda()
+        b.adjoint(res)
+        G = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+        b.gradient(G)
+        out[stride] = (G.cpu().numpy()[perm], mesh.batch_bytes(4, len(recs)), mesh.N)
+        b.close()
+        mesh.close()
+    Go_r = orc.ops.gradient(g_r, orc.mask)
+    Go_1 = orc.ops.gradient(g_1, orc.mask)
+    err = rel_l2(out[r][0], Go_r)
+    dep = rel_l2(Go_r, Go_1)
+    ring = lambda st: 4 * out[st][2] * 4 * (20 // st)
+    print(f"r = {r}: GPU vs oracle (subsampled) rel-L2 {err:.3e}; subsampled vs full gradient "
+          f"rel-L2 {dep:.3e}; recompute ring {ring(r) / 1e6:.2f} MB against {ring(1) / 1e6:.2f} MB; "
+          f"batch {out[r][1] / 1e6:.2f} MB against {out[1][1] / 1e6:.2f} MB")
+    assert err < GRAD_TOL
+    assert rel_l2(out[1][0], Go_1) < GRAD_TOL
+    assert out[r][1] < out[1][1]

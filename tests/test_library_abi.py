@@ -99,7 +99,7 @@ def test_inverted_cell_is_refused_with_einval():
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_point_outside_the_mesh_is_refused_with_einval(dim):
-    """Point location (Section 4.3) of a receiver outside the domain: FWI_EINVAL; points
+    """Point location (Section 4.2) of a receiver outside the domain: FWI_EINVAL; points
     inside (including a shared vertex) are found with reference coordinates that map back
     to the point."""
     import numpy as np

@@ -300,3 +300,28 @@ def test_manufactured_solution_converges_at_order_k_plus_1(k):
     print(f"KMV{k}tri: error {e8:.3e} (n=8), {e16:.3e} (n=16), observed order {order:.2f}")
     assert order > k + 0.85
     assert e16 < {2: 1e-4, 3: 3e-6, 4: 5e-8, 5: 2e-9}[k]
+
+
+def test_gradient_subsampling_weights_and_levels():
+    """Subsampling of the gradient's time sum (Section 3.6): the r phase-shifted subsampled
+    sums (offsets 0..r-1, weight r each) average exactly to the full sum, r = 1 is the full
+    sum, and the subsampled gradient departs from it by an amount that grows with r."""
+    m = _sq_mesh(3, 8)
+    X = m.coords
+    c = 1.6 + 0.4 * X[:, 1]
+    dt = 0.8 * wave.Operators(m, c, 1.0).cfl_dt()
+    nt = 240
+    ops = wave.Operators(m, c, dt)
+    H = assemble.point_matrix(m, np.array([[x, 0.85] for x in np.linspace(0.1, 0.9, 7)]))
+    w = analytic.ricker(np.arange(nt) * dt, 6.0)
+    rec, U = ops.forward(wave.point_source_rhs(m, [0.5, 0.2], w), nt, H, store=True)
+    res = 0.1 * rec
+    _, g1 = ops.adjoint(H, res, U_hist=U)
+    _, g1b = ops.adjoint(H, res, U_hist=U, r=1)
+    assert np.array_equal(g1, g1b)
+    errs = []
+    for r in (2, 4, 8):
+        parts = [ops.adjoint(H, res, U_hist=U, r=r, offset=o)[1] for o in range(r)]
+        assert np.allclose(np.mean(parts, axis=0), g1, rtol=0, atol=1e-13 * np.abs(g1).max())
+        errs.append(np.linalg.norm(parts[0] - g1) / np.linalg.norm(g1))
+    assert errs[0] < errs[1] < errs[2] < 0.5
