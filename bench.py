@@ -34,7 +34,9 @@ PEAK_HBM_FALLBACK = 6800.0
 METRIC = "DoF-steps/s (forward + adjoint, FP32, <=1e-5 rel-L2 vs FP64 oracle)"
 
 
-def workload_name(k):
+def workload_name(k, workload="marine2d"):
+    if workload == "thrust3d":
+        return f"thrust3d-5x5x3km-kmv{k}tet-layer0.75km-5Hz-3s"
     return f"marine2d-17x3.5km-kmv{k}-layer1km-5Hz-4s"
 
 
@@ -68,6 +70,41 @@ def make_workload(k=5, C=None, seed=0, nshots=40, nrec=500, T=4.0, f=5.0, small=
     lay["smax"] = signals.sigma_max(4.7, lay["width"])
     return dict(model=model, V=V, cells=cells, k=k, C=C, srcs=srcs, recs=recs, layer=lay, T=T,
                 f=f, box=box)
+
+
+def make_workload3d(k=2, seed=0, small=False, scale=1.0):
+    """The 3D workload (inputs only): the 5 km x 5 km x 3 km thrust model (layered, a thrust-
+    folded interface, two 5.5-6.0 km/s lenses, smooth perturbation; seeded stand-in for
+    Overthrust3D) with a 0.75 km damping layer on the sides and bottom, on a depth-graded
+    Kuhn tetrahedral mesh (40 m boxes in the top kilometre of slow rock, 60 m below; about
+    4.9M tetrahedra), 16 shots in a 4 x 4 grid at 50 m depth and a 100 x 100 receiver grid at
+    100 m depth, 5 Hz, 3 s. small=True: a 1.2 km x 1.2 km x 1.0 km box of the same model
+    (the oracle's sample). scale < 1 coarsens the boxes by that factor (for profiler
+    captures of the same kernels on a smaller case)."""
+    from synth import meshes, models, signals
+    model = models.Thrust3D(seed)
+    L = 0.75
+    if small:
+        xs = np.linspace(1.9, 3.1, 11)
+        zs = np.linspace(0.0, 1.0, 9)
+        V, cells = meshes.kuhn_tets(xs, xs, zs)
+        srcs = np.array([[2.5, 2.5, 0.05], [2.3, 2.6, 0.05], [2.6, 2.35, 0.05], [2.4, 2.4, 0.05]])
+        g = np.linspace(2.0, 3.0, 5)
+        recs = np.array([[x, y, 0.1] for x in g for y in g])
+        lay = dict(box=[(2.05, 2.95), (2.05, 2.95), (-10.0, 0.85)], faces=0b101111, width=0.15)
+    else:
+        xs = np.linspace(-L, 5 + L, int(round(108 * scale)) + 1)
+        zs = np.concatenate([np.arange(0.0, 1.0, 0.04 / scale),
+                             np.arange(1.0, 3.0 + L + 1e-9, 0.06 / scale)])
+        V, cells = meshes.kuhn_tets(xs, xs, zs)
+        g4 = np.linspace(1.0, 4.0, 4)
+        srcs = np.array([[x, y, 0.05] for x in g4 for y in g4])
+        g100 = np.linspace(0.05, 4.95, 100)
+        recs = np.array([[x, y, 0.1] for x in g100 for y in g100])
+        lay = dict(box=[(0.0, 5.0), (0.0, 5.0), (-10.0, 3.0)], faces=0b101111, width=L)
+    lay["smax"] = signals.sigma_max(6.0, lay["width"])
+    return dict(model=model, V=V, cells=cells, k=k, C=None, srcs=srcs, recs=recs, layer=lay,
+                T=3.0, f=5.0, dim=3)
 
 
 def shots_for_rank(nshots, S, rank, world, step=0):
@@ -128,17 +165,17 @@ class Clocks:
 _ORC = {}
 
 
-def _orc_init(k):
+def _orc_init(k, workload="marine2d"):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from parity_util import OracleCase
-    small = make_workload(k=k, small=True)
+    small = make_workload3d(k=k, small=True) if workload == "thrust3d" else make_workload(k=k, small=True)
     lay = small["layer"]
     probe = OracleCase(small["V"], small["cells"], k, small["model"], 1.0, 1, layer=lay,
                        absorbing=True, water=1.51)
     dt = 0.9 * probe.ops.cfl_dt()
     orc = OracleCase(small["V"], small["cells"], k, small["model"], dt, 1, layer=lay,
                      absorbing=True, water=1.51)
-    _ORC.update(k=k, small=small, dt=dt, orc=orc)
+    _ORC.update(k=k, small=small, dt=dt, orc=orc, workload=workload)
 
 
 def _orc_shot(job):
@@ -156,27 +193,29 @@ def _orc_shot(job):
     return (rec if keep else None), (g if keep else None), orc.mesh.N * nt * 2, el
 
 
-def oracle_pool(k, workers):
+def oracle_pool(k, workers, workload="marine2d"):
     import multiprocessing as mp
-    return mp.get_context("spawn").Pool(workers, initializer=_orc_init, initargs=(k,))
+    return mp.get_context("spawn").Pool(workers, initializer=_orc_init, initargs=(k, workload))
 
 
-def oracle_window_info(k):
-    _orc_init(k)
+def oracle_window_info(k, workload="marine2d"):
+    _orc_init(k, workload)
     return dict(dt=_ORC["dt"], N=_ORC["orc"].mesh.N, E=_ORC["small"]["cells"].shape[0],
                 small=_ORC["small"], orc=_ORC["orc"])
 
 
-def parity_shots(small, n):
+def parity_shots(small, n, workload="marine2d"):
     """n shot positions at 50 m depth across the small window."""
+    if workload == "thrust3d":
+        return np.stack([np.linspace(2.2, 2.8, n), np.linspace(2.7, 2.3, n), np.full(n, 0.05)], 1)
     return np.stack([np.linspace(6.3, 7.7, n), np.full(n, 0.05)], 1)
 
 
-def oracle_rate(pool, k, dt, workers, nsteps):
+def oracle_rate(pool, k, dt, workers, nsteps, workload="marine2d"):
     """DoF-steps/s of the FP64 oracle (forward + adjoint with the gradient integrand) over
     `workers` shots, one per worker, nsteps time steps each; wall-clock of the pool."""
     from synth import signals
-    srcs = parity_shots(None, workers)
+    srcs = parity_shots(None, workers, workload)
     wav = signals.ricker_samples(5.0, dt, nsteps).astype(np.float64)
     jobs = [(srcs[i], nsteps, wav, 0.03, False) for i in range(workers)]
     t0 = time.perf_counter()
@@ -192,69 +231,104 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def serving_stream(pkg, nreq=48, seed=0, budget_gb=16.0, interarrivals=(0.008, 0.004, 0.002)):
-    """Poisson streams of shot requests over six resident meshes (structured triangle meshes
-    of 20k-180k elements, KMV2..5, 300-step records; half of the requests carry observed data
-    and ask for the gradient), at three mean inter-arrival times. Each stream is served twice:
-    by the continuous-batching server (up to 4 shots of one mesh per launch sequence, two
-    workers) and in the one-shot-per-launch form (one worker, one shot per batch). Returns
-    shots/s and p50/p99 latency per stream."""
-    from paper_2108_10946_gb300.serving import Request, ShotServer
-    from synth import meshes, models, signals
-    rng = np.random.default_rng(seed)
-    specs = [(100, 2, 8.0), (140, 3, 6.0), (180, 4, 5.0), (220, 5, 4.0), (260, 3, 3.0),
-             (300, 2, 8.0)]
+# Shot-server pool shaped like the serving workload: six seeded 2D meshes of 50k-2M
+# triangles, KMV2..5, 3-8 Hz peaks and 2-6 s records. Each mesh is a structured
+# right-triangle mesh of a square whose cell size follows the paper's cells per wavelength
+# for 5 % error (Table gwpl: C = 5.85, 3.08, 2.22, 1.69 for KMV2..5) at the slowest speed
+# 1.4 km/s and the mesh's peak frequency; c(x) a smooth 1.4-3.0 km/s model.
+SERVING_POOL = [  # (triangles, k, peak Hz, record s)
+    (50_000, 5, 8.0, 2.0), (120_000, 3, 6.0, 3.0), (250_000, 4, 5.0, 4.0),
+    (500_000, 2, 4.0, 5.0), (1_000_000, 3, 3.0, 3.0), (2_000_000, 2, 3.0, 6.0)]
+CELLS_PER_WAVELENGTH = {2: 5.85, 3: 3.08, 4: 2.22, 5: 1.69}
+
+
+def serving_pool(pkg, scale=1.0):
+    from synth import meshes, models
     pool = {}
-    for i, (n, k, f) in enumerate(specs):
-        V, C = meshes.structured_tri(n, n, 2.0, 2.0)
+    for i, (E, k, f, T) in enumerate(SERVING_POOL):
+        n = max(8, int(round(np.sqrt(scale * E / 2))))
+        h = 1.4 / f / CELLS_PER_WAVELENGTH[k]
+        L = n * h
+        V, C = meshes.structured_tri(n, n, L, L)
+        cfun = lambda X, L=L: models.smooth2d(X / L * 2.0)
         probe = pkg.Mesh(V, C, k, 1, dt=0.0, cfl_factor=0.8)
-        probe.set_velocity(models.smooth2d(probe.dof_coords() / 2.0))
+        probe.set_velocity(cfun(probe.dof_coords()))
         dt = probe.dt
         probe.close()
-        m = pkg.Mesh(V, C, k, 300, dt=dt, ckpt_stride=30, absorbing=True)
-        m.set_velocity(models.smooth2d(m.dof_coords() / 2.0))
-        recs = np.stack([np.linspace(0.1, 1.9, 50), np.full(50, 1.8)], 1)
-        pool[f"m{i}"] = (m, recs, f)
-    meshes_ = {name: (m, recs) for name, (m, recs, f) in pool.items()}
+        nt = int(round(T / dt))
+        m = pkg.Mesh(V, C, k, nt, dt=dt, ckpt_stride=50, absorbing=True)
+        m.set_velocity(cfun(m.dof_coords()))
+        recs = np.stack([np.linspace(0.05 * L, 0.95 * L, 50), np.full(50, 0.9 * L)], 1)
+        pool[f"m{i}"] = dict(mesh=m, recs=recs, f=f, L=L, E=2 * n * n, k=k, T=T)
+    return pool
 
-    def make_plan(mean_gap):
-        arrivals = np.cumsum(rng.exponential(mean_gap, nreq))
+
+def serving_stream(pkg, nreq=32, seed=0, budget_gb=40.0, loads=(0.5, 0.75, 1.0, 1.25, 1.5),
+                   scale=1.0):
+    """Poisson streams of shot requests over the six resident meshes of SERVING_POOL (each
+    request on a random mesh; half carry observed records and ask for their own gradient).
+    The batched server's saturation throughput is measured first (all requests at once);
+    then streams at 0.5x-1.5x of it are each served twice: by the continuous-batching server
+    (rolling forward batches with admission every 50 steps, gradient batches, up to 4 shots
+    per batch, two workers) and in the one-shot-per-launch form (one worker, one shot per
+    batch, whole records). Returns shots/s and p50/p99 latency per stream."""
+    from paper_2108_10946_gb300.serving import Request, ShotServer
+    from synth import signals
+    rng = np.random.default_rng(seed)
+    t_setup = time.perf_counter()
+    pool = serving_pool(pkg, scale)
+    t_setup = time.perf_counter() - t_setup
+    meshes_ = {name: (p["mesh"], p["recs"]) for name, p in pool.items()}
+    names = sorted(pool)
+
+    def make_plan(rate):
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq)
         plan = []
         for i in range(nreq):
-            name = f"m{rng.integers(len(specs))}"
-            m, recs, f = pool[name]
+            mi = int(rng.integers(len(names)))
+            p = pool[names[mi]]
+            m, f, L = p["mesh"], p["f"], p["L"]
             wav = signals.ricker_samples(f, m.dt, m.nsteps, t0=1.2 / f)
-            obs = np.zeros((m.nsteps + 1, len(recs)), np.float32) if rng.random() < 0.5 else None
-            plan.append((arrivals[i], name, [rng.uniform(0.2, 1.8), rng.uniform(0.1, 0.5)], wav, obs))
+            obs = np.zeros((m.nsteps + 1, len(p["recs"])), np.float32) if rng.random() < 0.5 else None
+            src = [rng.uniform(0.1, 0.9) * L, rng.uniform(0.05, 0.3) * L]
+            plan.append((arrivals[i], mi, src, wav, obs))
         return plan
 
-    def serve(plan, max_batch, workers):
+    def serve(plan, max_batch, workers, rolling):
         srv = ShotServer(meshes_, hbm_budget_bytes=int(budget_gb * 2 ** 30), max_batch=max_batch,
-                         workers=workers)
+                         workers=workers, rolling=rolling)
         t0 = time.perf_counter()
         reqs = []
-        for i, (t, name, src, wav, obs) in enumerate(plan):
+        for i, (t, mi, src, wav, obs) in enumerate(plan):
             now = time.perf_counter() - t0
             if t > now:
                 time.sleep(t - now)
-            reqs.append(srv.submit(Request(i, name, src, wav, observed=obs)))
+            reqs.append(srv.submit(Request(i, names[mi], src, wav, observed=obs)))
         for r in reqs:
-            r.event.wait(600)
+            r.event.wait(900)
         st = srv.stats()
+        st["errors"] = sum(r.error is not None for r in reqs)
+        st["wall_s"] = time.perf_counter() - t0
         srv.close()
         return st
 
-    serve(make_plan(interarrivals[0]), 4, 2)  # warm-up: resident batches, code paths
+    serve(make_plan(0), 4, 2, True)  # warm-up: resident batches, code paths
+    sat = serve(make_plan(0), 4, 2, True)
+    sat_one = serve(make_plan(0), 1, 1, False)
+    lam = sat["shots_per_s"]
     streams = []
-    for gap in interarrivals:
-        plan = make_plan(gap)
-        streams.append({"mean_interarrival_s": gap, "batched": serve(plan, 4, 2),
-                        "one_shot_per_launch": serve(plan, 1, 1)})
-    for m, _, _ in pool.values():
-        m.close()
-    return {"requests_per_stream": nreq,
-            "meshes": "6 structured 2D meshes, 20k-180k triangles, KMV2-5",
-            "record_steps": 300, "gradient_fraction": "1/2", "streams": streams}
+    for rho in loads:
+        plan = make_plan(rho * lam)
+        streams.append({"load": rho, "mean_interarrival_s": 1.0 / (rho * lam),
+                        "batched": serve(plan, 4, 2, True),
+                        "one_shot_per_launch": serve(plan, 1, 1, False)})
+    desc = [{"triangles": p["E"], "k": p["k"], "peak_hz": p["f"], "record_s": p["T"],
+             "steps": p["mesh"].nsteps, "dofs": p["mesh"].N} for p in pool.values()]
+    for p in pool.values():
+        p["mesh"].close()
+    return {"requests_per_stream": nreq, "meshes": desc, "gradient_fraction": "1/2",
+            "setup_s": t_setup, "saturation": {"batched": sat, "one_shot_per_launch": sat_one},
+            "streams": streams}
 
 
 def run_reference(args):
@@ -266,28 +340,30 @@ def run_reference(args):
         return
     k = args.k
     cores = host_cores()
-    info = oracle_window_info(k)
-    pool = oracle_pool(k, cores)
+    info = oracle_window_info(k, args.workload)
+    pool = oracle_pool(k, cores, args.workload)
     try:
         for _ in range(args.warmup):
-            oracle_rate(pool, k, info["dt"], cores, args.ref_steps)
+            oracle_rate(pool, k, info["dt"], cores, args.ref_steps, args.workload)
         vals = []
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            vals.append(oracle_rate(pool, k, info["dt"], cores, args.ref_steps)["value"])
+            vals.append(oracle_rate(pool, k, info["dt"], cores, args.ref_steps, args.workload)["value"])
         el = time.perf_counter() - t0
     finally:
         pool.close()
         pool.join()
     v = float(np.mean(vals))
-    sample = (f"FP64 oracle, KMV{k}tri on the 2 km x 1.5 km marine window of the workload "
+    where = ("a 1.2 km x 1.2 km x 1.0 km box of the thrust model" if args.workload == "thrust3d"
+             else "the 2 km x 1.5 km marine window")
+    sample = (f"FP64 oracle, KMV{k}{'tet' if args.workload == 'thrust3d' else 'tri'} on {where} of the workload "
               f"({info['E']} elements, N={info['N']}), {cores} shots (one per host core), "
               f"{args.ref_steps} forward + adjoint steps each per bench step")
     line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * el / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(k),
+            "config": {"workload": workload_name(k, args.workload),
                        "sample": "the FP64 oracle on the host cores, timed on a bounded window of "
                                  "the workload (see cpu_baseline.sample)"},
             "cpu_baseline": {"value": v, "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
@@ -296,7 +372,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def parity_sample(pkg, pool, info, k, S, T_par):
+def parity_sample(pkg, pool, info, k, S, T_par, workload="marine2d"):
     """The GPU library against the FP64 oracle on the workload's small marine window (same
     mesher, model, water, layer and absorbing boundary; S shots, T_par seconds): records
     rel-L2 (worst shot) and gradient rel-L2, as the tests measure them. The oracle shots run
@@ -307,7 +383,7 @@ def parity_sample(pkg, pool, info, k, S, T_par):
     from parity_util import match_dofs, rel_l2
     dt, small, orc = info["dt"], info["small"], info["orc"]
     nt = int(round(T_par / dt))
-    srcs = parity_shots(small, S)
+    srcs = parity_shots(small, S, workload)
     wav = signals.ricker_samples(5.0, dt, nt).astype(np.float32)
     out = pool.map(_orc_shot, [(srcs[i], nt, wav.astype(np.float64), 0.03, True) for i in range(S)])
     lay = small["layer"]
@@ -331,24 +407,28 @@ def parity_sample(pkg, pool, info, k, S, T_par):
     b.close()
     mesh.close()
     return {"records_rel_l2_max": rec_err, "gradient_rel_l2": g_err, "shots": S, "steps": nt,
-            "window": f"2 km x 1.5 km marine window, KMV{k}, N={info['N']}, {T_par} s, water, "
-                      f"layer, absorbing boundary, residual 0.03 d"}
+            "window": (f"1.2 km x 1.2 km x 1.0 km box of the thrust model, KMV{k}tet" if workload == "thrust3d"
+                       else f"2 km x 1.5 km marine window, KMV{k}") +
+                      f", N={info['N']}, {T_par} s, layer, absorbing boundary, residual 0.03 d"}
 
 
 NODES = {2: (7, 6), 3: (12, 9), 4: (18, 12), 5: (30, 15)}  # KMVktri: nodes, shared nodes
+NODES3 = {2: (15, 14), 3: (32, 28)}                           # KMVktet
 
 
-def step_roofline(prof, k, E, N, S, fp32_tflops, sm_count, peaks, src):
+def step_roofline(prof, k, E, N, S, fp32_tflops, sm_count, peaks, src, dim=2):
     """Roofline entries of the forward time step (element kernels + shared-DoF kernel) and of
     the adjoint step with the gradient integrand, from per-step CUDA-event times.
     Algorithmic work per step (stated in DESIGN):
       forward flops = E S 4 d n^2 (two n x n contractions per direction per element and shot)
       adjoint flops = E S 6 d n^2 (plus the contraction of the forward field)
-      forward bytes = N (16 S + 8) + E (4 n_s + 12): u, v read and written per shot, c^2 and
-                      M^-1 per DoF, shared-node connectivity and Ghat per element
+      forward bytes = N (16 S + 8) + E (4 n_s + 4 n_g): u, v read and written per shot, c^2
+                      and M^-1 per DoF, shared-node connectivity and Ghat (n_g = 3 in 2D, 6 in
+                      3D) per element
       adjoint bytes = forward bytes + 4 N S (forward field) + 8 N (gradient segment)"""
-    nn, ns = NODES[k]
-    d = 2
+    nn, ns = (NODES if dim == 2 else NODES3)[k]
+    d = dim
+    ng = 3 if dim == 2 else 6  # Ghat entries per element
     fs, as_ = max(prof["fwd_steps"], 1), max(prof["adj_steps"], 1)
     fwd_ms = (prof["fwd_elem_ms"] + prof["fwd_node_ms"]) / fs
     adj_ms = (prof["adj_elem_ms"] + prof["adj_node_ms"]) / as_
@@ -370,7 +450,7 @@ def step_roofline(prof, k, E, N, S, fp32_tflops, sm_count, peaks, src):
                   "flops_per_step": flops, "bytes_per_step": nbytes})
         return e
 
-    fwd_bytes = N * (16 * S + 8) + E * (4 * ns + 12)
+    fwd_bytes = N * (16 * S + 8) + E * (4 * ns + 4 * ng)
     roof = entry(E * S * 4 * d * nn * nn, fwd_bytes, fwd_ms,
                  "forward time step (element kernels + shared-DoF kernel)")
     roof["element_kernel_us"] = prof["fwd_elem_ms"] / fs * 1e3
@@ -451,11 +531,12 @@ def run_ours(args):
     pkg.build()
     pool = info = None
     cores = host_cores()
+    three_d = args.workload == "thrust3d"
     if rank == 0 and not args.no_cpu_baseline:
         # the oracle's worker pool starts now (spawn) and builds its window while the GPU runs
-        pool = oracle_pool(args.k, cores)
+        pool = oracle_pool(args.k, cores, args.workload)
     fp32_tflops, sm_count = pkg.lib.fp32_peak()
-    wl = make_workload(k=args.k, C=args.C)
+    wl = make_workload3d(k=args.k, scale=args.mesh_scale) if three_d else make_workload(k=args.k, C=args.C)
     lay = wl["layer"]
     t_setup = time.perf_counter()
     mesh = pkg.Mesh(wl["V"], wl["cells"], wl["k"], 1, dt=0.0, cfl_factor=0.9,
@@ -548,10 +629,11 @@ def run_ours(args):
     batch.profile(False)
     peaks, src = _peaks()
     clk_sum = clk.summary(local)
-    roof = step_roofline(prof, wl["k"], E, N, S, fp32_tflops, sm_count, peaks, src)
+    roof = step_roofline(prof, wl["k"], E, N, S, fp32_tflops, sm_count, peaks, src,
+                         dim=3 if three_d else 2)
 
     extra_k = []
-    if rank == 0 and args.extra_k:
+    if rank == 0 and args.extra_k and not three_d:
         for kx in [int(x) for x in args.extra_k.split(",") if x]:
             extra_k.append(degree_line(pkg, kx, args, S, fp32_tflops, sm_count, peaks, src))
 
@@ -588,20 +670,23 @@ def run_ours(args):
         mp_.close()
 
     serving = None
-    if rank == 0 and not args.no_serving:
-        serving = serving_stream(pkg)
+    if rank == 0 and not args.no_serving and not three_d:
+        serving = serving_stream(pkg, scale=args.serving_scale)
 
     cpu = parity = None
     if pool is not None:
         try:
-            info = oracle_window_info(wl["k"])
-            parity = parity_sample(pkg, pool, info, wl["k"], S, {2: 1.0, 3: 0.8, 4: 0.5, 5: 0.3}[wl["k"]])
-            ob = oracle_rate(pool, wl["k"], info["dt"], cores, args.ref_steps)
+            info = oracle_window_info(wl["k"], args.workload)
+            T_par = 0.6 if three_d else {2: 1.0, 3: 0.8, 4: 0.5, 5: 0.3}[wl["k"]]
+            parity = parity_sample(pkg, pool, info, wl["k"], S, T_par, args.workload)
+            ob = oracle_rate(pool, wl["k"], info["dt"], cores, args.ref_steps, args.workload)
         finally:
             pool.close()
             pool.join()
+        where = ("a 1.2 km x 1.2 km x 1.0 km box of the thrust model" if three_d else
+                 "the 2 km x 1.5 km marine window")
         cpu = {"value": ob["value"], "unit": "DoF-steps/s", "cores": cores, "kind": "oracle",
-               "sample": (f"FP64 oracle, KMV{wl['k']}tri on the 2 km x 1.5 km marine window of the "
+               "sample": (f"FP64 oracle, KMV{wl['k']}{'tet' if three_d else 'tri'} on {where} of the "
                           f"workload ({info['E']} elements, N={info['N']}), {cores} shots in "
                           f"parallel (one per host core), {ob['nsteps']} forward + adjoint steps each, "
                           f"{ob['seconds']:.1f} s wall")}
@@ -611,7 +696,7 @@ def run_ours(args):
             "value": value, "unit": "DoF-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(wl["k"]),
+            "config": {"workload": workload_name(wl["k"], args.workload),
                        "elements": E, "dofs": N, "dt": dt, "record_steps": nt_record,
                        "window_steps": nt, "shots_per_step": S,
                        "receivers": R, "ckpt_stride": args.ckpt, "C": wl["C"],
@@ -641,7 +726,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--workload", default="marine2d", choices=["marine2d", "thrust3d"],
+                    help="marine2d: the 2D marine section (KMV2-5 triangles); thrust3d: the 3D "
+                         "thrust section (KMV2/3 tetrahedra, use --k 2 or 3)")
+    ap.add_argument("--mesh-scale", type=float, default=1.0,
+                    help="thrust3d only: coarsen the mesh's boxes by this factor (< 1 for captures)")
+    ap.add_argument("--k", type=int, default=None,
+                    help="element degree (default 5 for marine2d, 2 for thrust3d)")
     ap.add_argument("--C", type=float, default=None)
     ap.add_argument("--shots", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=50)
@@ -652,12 +743,18 @@ def main():
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream latency run")
+    ap.add_argument("--serving-scale", type=float, default=1.0,
+                    help="element-count factor of the serving pool (1 = 50k-2M triangles)")
     ap.add_argument("--extra-k", default="3,4",
                     help="other element degrees measured on the same workload (comma list; '' for none)")
     ap.add_argument("--extra-window", type=int, default=500)
     ap.add_argument("--ref-steps", type=int, default=300,
                     help="time steps per shot of the oracle's timed sample")
     args = ap.parse_args()
+    if args.k is None:
+        args.k = 2 if args.workload == "thrust3d" else 5
+    if args.workload == "thrust3d" and args.ref_steps == 300:
+        args.ref_steps = 100  # the KMV3tet oracle takes about 0.17 s per step and shot
     if args.impl == "reference":
         run_reference(args)
     elif args.gpus > 1 and "WORLD_SIZE" not in os.environ:

@@ -217,11 +217,31 @@ int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* s
  *     before it returns. */
 int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out, void* stream);
 
+/* Continuous batching inside a record (Section 4.5: the shots of a batch are independent
+ * lanes of the same time steps). Advances the batch's forward state by nseg steps
+ * (1 <= nseg <= the mesh's nsteps), each lane at its own point of its own shot, so that a
+ * caller can start a new shot in a lane that freed up without waiting for the others.
+ *   - reset_mask: bit s set = lane s starts a new shot; its wavefield and damping-layer
+ *     state are set to zero before the first step. Bits at or above S are an error
+ *     (FWI_EINVAL). Other lanes continue from where the last call left them.
+ *   - wavelet[S][nseg] (host or device): each lane's source samples for these nseg steps,
+ *     i.e. samples t .. t+nseg-1 of that lane's wavelet when the lane stands at step t of its
+ *     shot (zeros for an idle lane).
+ *   - rec_out[S][nseg+1][R] (host or device, may be NULL): each lane's receiver samples at
+ *     the nseg + 1 time levels the call spans, from the level it starts on to the level it
+ *     ends on (consecutive calls share one level).
+ *   - A lane's records equal those of fwi_forward_shot for the same wavelet, up to the
+ *     summation order of FP32 atomics. No checkpoints are stored: after this call the next
+ *     fwi_adjoint_* needs a fresh fwi_forward_shot.
+ *   - Synchronises the stream before it returns, like every solve here. */
+int fwi_forward_segment(fwi_batch* b, int nseg, uint32_t reset_mask, const float* wavelet,
+                        float* rec_out, void* stream);
+
 /* Discrete adjoint solve (Section 3.5, the transposed recurrence run backwards) driven by
  * residual[S][Nt+1][R] = d - dtilde, with the forward wavefield recomputed segment by
  * segment from the checkpoints of the last fwi_forward_shot. Accumulates the integrand of
- * Eq. (gradient3), sum_n 2 c grad u^dagger . grad u, summed over the batch's shots, into
- * the batch's compensated FP64 accumulator, and J = 1/2 sum residual^2. */
+ * Eq. (gradient3), sum_n 2 c grad u^dagger . grad u, of each shot into that shot's
+ * compensated FP64 accumulator, and each shot's J = 1/2 sum residual^2. */
 int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream);
 
 /* The same adjoint solve for the L2 misfit of Eq. (l2error): the residual d - dtilde is
@@ -233,6 +253,23 @@ int fwi_adjoint_misfit(fwi_batch* b, const float* observed, void* stream);
  * grad_out[N] doubles in DoF order, misfit_out (may be NULL) the accumulated J. Clears
  * the accumulators. */
 int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream);
+
+/* The shots' own gradients, for callers that batch independent requests (Section 4.5: one
+ * gradient per shot, summed over shots by whoever needs the total): grad_out[S][N] doubles
+ * (host or device), lane s holding G_s = M^{-1} g_s masked like fwi_gradient; misfit_out
+ * (host, may be NULL) gets S doubles, J_s of each shot. The sum over lanes equals what
+ * fwi_gradient returns. The adjoint calls must have run with fwi_batch_set_gradient_lanes
+ * (b, 1), else FWI_EINVAL; with no adjoint since the last clear the lanes are zero. Clears
+ * the accumulators. */
+int fwi_gradient_lanes(fwi_batch* b, double* grad_out, double* misfit_out, void* stream);
+
+/* Whether the adjoint calls keep each shot's gradient integrand in its own accumulator
+ * (per_shot = 1, needed by fwi_gradient_lanes) or sum the shots as they go (0, the default:
+ * one accumulator of N values, fewer memory operations per gradient step). The setting
+ * applies from the next fwi_adjoint_* call; changing it while the accumulators hold sums of
+ * the other kind (an adjoint ran and no fwi_gradient* cleared them) makes that call return
+ * FWI_EINVAL. The batch's device memory is sized for the per-shot form either way. */
+int fwi_batch_set_gradient_lanes(fwi_batch* b, int per_shot);
 
 /* Per-kernel timing (tracing): when enabled, every time step of the batch's forward,
  * recompute and adjoint loops is bracketed by CUDA events on the call's stream. */

@@ -180,8 +180,8 @@ struct fwi_batch {
   float *ua = nullptr, *va = nullptr, *Pa = nullptr, *Ya = nullptr;  // adjoint state
   float* ckpt = nullptr;   // C x state
   float* ring = nullptr;   // K x [N][S]
-  float* gseg = nullptr;
-  double *gsum = nullptr, *gcomp = nullptr, *misfit = nullptr;
+  float* gseg = nullptr;                                   // [S][N] FP32 segment sums
+  double *gsum = nullptr, *gcomp = nullptr, *misfit = nullptr;  // [S][N], [S][N], [S]
   int* status = nullptr;
   cudaStream_t st2 = nullptr;  // second stream of the chunked step (layer chunks)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -195,6 +195,8 @@ struct fwi_batch {
   bool forward_done = false;
   int launch_error = 0;  // first kernel configuration error of a call (cudaError_t)
   int tc_wait_limit = 1 << 22;  // polls of each bounded wait of the tensor-core kernel
+  int grad_lanes = 0;           // 1: the next adjoint keeps each shot's gradient apart
+  int acc_lanes = -1;           // what the accumulators hold: -1 nothing, 0 summed, 1 per shot
   // optional per-kernel timing with CUDA events (fwi_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -1139,9 +1141,9 @@ int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const
       (rc = dalloc(&b->Y, YS)) || (rc = dalloc(&b->Yacc, YS)) || (rc = dalloc(&b->ua, NS_)) ||
       (rc = dalloc(&b->va, NS_)) || (rc = dalloc(&b->Pa, LS)) || (rc = dalloc(&b->Ya, YS)) ||
       (rc = dalloc(&b->ckpt, b->state_floats() * b->C)) ||
-      (rc = dalloc(&b->ring, NS_ * (b->K / b->gstride))) || (rc = dalloc(&b->gseg, (size_t)N)) ||
-      (rc = dalloc(&b->gsum, (size_t)N)) || (rc = dalloc(&b->gcomp, (size_t)N)) ||
-      (rc = dalloc(&b->misfit, 1)) || (rc = dalloc(&b->status, 1)))
+      (rc = dalloc(&b->ring, NS_ * (b->K / b->gstride))) || (rc = dalloc(&b->gseg, NS_)) ||
+      (rc = dalloc(&b->gsum, NS_)) || (rc = dalloc(&b->gcomp, NS_)) ||
+      (rc = dalloc(&b->misfit, (size_t)S)) || (rc = dalloc(&b->status, 1)))
     return rc;
   if (m->layout == 0) {
     CUDA_TRY(cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking));
@@ -1154,10 +1156,10 @@ int fwi_batch_create(fwi_mesh* m, int nshots, const double* src, int nrec, const
     CUDA_TRY(cudaMemset(b->PaccY, 0, LS * sizeof(float)));
     CUDA_TRY(cudaMemset(b->Yacc, 0, YS * sizeof(float)));
   }
-  CUDA_TRY(cudaMemset(b->gseg, 0, (size_t)N * sizeof(float)));
-  CUDA_TRY(cudaMemset(b->gsum, 0, (size_t)N * sizeof(double)));
-  CUDA_TRY(cudaMemset(b->gcomp, 0, (size_t)N * sizeof(double)));
-  CUDA_TRY(cudaMemset(b->misfit, 0, sizeof(double)));
+  CUDA_TRY(cudaMemset(b->gseg, 0, NS_ * sizeof(float)));
+  CUDA_TRY(cudaMemset(b->gsum, 0, NS_ * sizeof(double)));
+  CUDA_TRY(cudaMemset(b->gcomp, 0, NS_ * sizeof(double)));
+  CUDA_TRY(cudaMemset(b->misfit, 0, (size_t)S * sizeof(double)));
   CUDA_TRY(cudaMemset(b->status, 0, sizeof(int)));
   *out = b.release();
   return 0;
@@ -1221,6 +1223,7 @@ StepArgs base_args(fwi_batch* b) {
   a.rslot_phi = b->d_rslot_phi;
   a.R = b->R;
   a.gseg = b->gseg;
+  a.grad_lanes = b->grad_lanes;
   a.status = b->status;
   a.tc_wait_limit = b->tc_wait_limit;
   return a;
@@ -1337,10 +1340,12 @@ int check_status(fwi_batch* b, cudaStream_t st) {
 }
 
 // Forward steps n0 .. n1-1 on the batch's forward state; optional records and checkpoints.
+// window > 0: wav is [S][window] and recs [S][window+1][R] (the steps of one segment).
 void forward_steps(fwi_batch* b, int n0, int n1, const float* wav, float* recs, bool ckpts,
-                   cudaStream_t st, float* r_scratch = nullptr) {
+                   cudaStream_t st, float* r_scratch = nullptr, int window = 0) {
   StepArgs a = base_args(b);
   if (r_scratch) a.r = r_scratch;
+  if (window > 0) a.nt = window;
   a.mode = 0;
   a.tc = 0;  // forward and recompute steps always on FP32 CUDA cores (records within 1e-5)
   a.u = b->u;
@@ -1400,8 +1405,12 @@ int fwi_forward_shot(fwi_batch* b, const float* wavelet, float* rec_out, void* s
 namespace {
 // Adjoint + gradient accumulation for a device residual [S][nt+1][R].
 int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
+  if (b->acc_lanes >= 0 && b->acc_lanes != b->grad_lanes)
+    return fail(FWI_EINVAL, "the gradient accumulators hold sums of the other kind: call "
+                            "fwi_gradient* before changing fwi_batch_set_gradient_lanes");
+  b->acc_lanes = b->grad_lanes;
   const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
-  fwi::launch_misfit(res, (int64_t)rn, b->misfit, st);
+  fwi::launch_misfit(res, (int64_t)rn / b->S, b->S, b->misfit, st);
   g_launches += 1;
   StepArgs a = base_args(b);
   a.mode = 1;
@@ -1437,7 +1446,8 @@ int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
       a.ring_u = mm % r == 0 ? b->ring + NS_ * (size_t)((mm - n0) / r) : nullptr;
       run_step(b, a, st);
     }
-    fwi::launch_fold(b->gseg, b->gsum, b->gcomp, b->m->N, (double)r, st);
+    fwi::launch_fold(b->gseg, b->gsum, b->gcomp, (int64_t)b->m->N * (b->grad_lanes ? b->S : 1),
+                     (double)r, st);
     g_launches += 1;
   }
   return check_status(b, st);
@@ -1528,6 +1538,49 @@ int fwi_forward_shot_noalloc(fwi_batch* b, const float* wavelet, float* rec_out,
   return check_status(b, st);
 }
 
+int fwi_forward_segment(fwi_batch* b, int nseg, uint32_t reset_mask, const float* wavelet,
+                        float* rec_out, void* stream) {
+  if (!b || !wavelet) return fail(FWI_EINVAL, "fwi_forward_segment: null argument");
+  if (int rc = check_device(b->m)) return rc;
+  if (nseg < 1 || nseg > b->nt)
+    return fail(FWI_EINVAL, "fwi_forward_segment: nseg must lie in 1 .. nsteps");
+  if (b->S < 32 && (reset_mask >> b->S) != 0)
+    return fail(FWI_EINVAL, "fwi_forward_segment: reset_mask names a lane beyond the batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const fwi_mesh* m = b->m;
+  const size_t wn = (size_t)b->S * nseg, rn = (size_t)b->S * (nseg + 1) * b->R;
+  if (!b->wav_dev && dalloc(&b->wav_dev, (size_t)b->S * b->nt)) return FWI_ENOMEM;
+  const size_t rfull = (size_t)b->S * (b->nt + 1) * b->R;
+  if (!b->rec_dev && dalloc(&b->rec_dev, rfull ? rfull : 1)) return FWI_ENOMEM;
+  CUDA_TRY(cudaMemcpyAsync(b->wav_dev, wavelet, wn * sizeof(float),
+                           is_device_ptr(wavelet) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // the batch's checkpoints no longer describe its forward state
+  b->forward_done = false;
+  if (reset_mask) {
+    const int S = b->S;
+    fwi::launch_lane_reset(b->u, m->N, S, reset_mask, st);
+    fwi::launch_lane_reset(b->v, m->N, S, reset_mask, st);
+    fwi::launch_lane_reset(b->P, (int64_t)m->Nl * m->dim, S, reset_mask, st);
+    fwi::launch_lane_reset(b->Y, m->Nl, S, reset_mask, st);
+    g_launches += 2 + (m->Nl > 0 ? 2 : 0);
+  }
+  if (rn) CUDA_TRY(cudaMemsetAsync(b->rec_dev, 0, rn * sizeof(float), st));
+  forward_steps(b, 0, nseg, b->wav_dev, b->rec_dev, false, st, nullptr, nseg);
+  if (b->R) {
+    StepArgs a = base_args(b);
+    a.u = b->u;
+    a.rec = b->rec_dev;
+    a.nt = nseg;
+    a.n = nseg;
+    m->ks->launch_record(a, b->d_rec_elem, b->d_rec_phi, st);
+    g_launches += 1;
+  }
+  if (rec_out && rn)
+    CUDA_TRY(cudaMemcpyAsync(rec_out, b->rec_dev, rn * sizeof(float),
+                             is_device_ptr(rec_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  return check_status(b, st);
+}
+
 int fwi_adjoint_shot(fwi_batch* b, const float* residual, void* stream) {
   if (!b || !residual) return fail(FWI_EINVAL, "fwi_adjoint_shot: null argument");
   if (!b->forward_done) return fail(FWI_EINVAL, "fwi_adjoint_shot needs a preceding fwi_forward_shot");
@@ -1552,29 +1605,69 @@ int fwi_adjoint_misfit(fwi_batch* b, const float* observed, void* stream) {
   return adjoint_device(b, b->res_dev, st);
 }
 
-int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream) {
-  if (!b || !grad_out) return fail(FWI_EINVAL, "fwi_gradient: null argument");
+}  // extern "C"
+
+namespace {
+// G = M^-1 g (M = the lumped mass; nullptr for the raw dJ/dc), masked, summed over the
+// batch's shots or per shot ([S][N]); misfit_out gets J (summed, or [S] per shot). Clears the
+// accumulators. out and misfit_out may be host or device memory (misfit_out host only).
+int finish_gradient(fwi_batch* b, double* out_user, double* misfit_out, const double* M,
+                    bool per_lane, cudaStream_t st, const char* name) {
+  if (!b || !out_user) return fail(FWI_EINVAL, std::string(name) + ": null argument");
   if (int rc = check_device(b->m)) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int N = b->m->N;
-  double* out = grad_out;
-  const bool host = !is_device_ptr(grad_out);
+  if (per_lane && b->acc_lanes == 0)
+    return fail(FWI_EINVAL, std::string(name) + ": the adjoint summed the shots' gradients; call "
+                            "fwi_batch_set_gradient_lanes(b, 1) before it");
+  const int N = b->m->N, S = b->S;
+  const int lanes = b->acc_lanes == 1 ? S : 1;  // rows the accumulators hold
+  const size_t count = per_lane ? (size_t)N * S : (size_t)N;
+  double* out = out_user;
+  const bool host = !is_device_ptr(out_user);
   if (host) {
-    if (!b->stage_grad && dalloc(&b->stage_grad, (size_t)N)) return FWI_ENOMEM;
+    if (!b->stage_grad && dalloc(&b->stage_grad, (size_t)N * S)) return FWI_ENOMEM;
     out = b->stage_grad;
   }
-  fwi::launch_finish_gradient(b->gsum, b->gcomp, nullptr, b->m->d_M, b->m->d_mask, out, N, st);
-  g_launches += 1;
-  if (host) CUDA_TRY(cudaMemcpyAsync(grad_out, out, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
-  double J = 0;
-  CUDA_TRY(cudaMemcpyAsync(&J, b->misfit, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (per_lane && b->acc_lanes != 1) {  // nothing accumulated since the last clear: zeros
+    CUDA_TRY(cudaMemsetAsync(out, 0, count * sizeof(double), st));
+  } else {
+    fwi::launch_finish_gradient(b->gsum, b->gcomp, nullptr, M, b->m->d_mask, out, N, lanes,
+                                per_lane ? 1 : 0, st);
+    g_launches += 1;
+  }
+  if (host)
+    CUDA_TRY(cudaMemcpyAsync(out_user, out, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> J(S, 0.0);
+  CUDA_TRY(cudaMemcpyAsync(J.data(), b->misfit, S * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  if (misfit_out) *misfit_out = J;
-  CUDA_TRY(cudaMemsetAsync(b->gsum, 0, (size_t)N * sizeof(double), st));
-  CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, (size_t)N * sizeof(double), st));
-  CUDA_TRY(cudaMemsetAsync(b->misfit, 0, sizeof(double), st));
+  if (misfit_out) {
+    if (per_lane) {
+      for (int s = 0; s < S; ++s) misfit_out[s] = J[s];
+    } else {
+      double t = 0;
+      for (double v : J) t += v;
+      *misfit_out = t;
+    }
+  }
+  const size_t NS_ = (size_t)N * S;
+  CUDA_TRY(cudaMemsetAsync(b->gsum, 0, NS_ * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, NS_ * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->misfit, 0, S * sizeof(double), st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  b->acc_lanes = -1;
   return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int fwi_gradient(fwi_batch* b, double* grad_out, double* misfit_out, void* stream) {
+  return finish_gradient(b, grad_out, misfit_out, b ? b->m->d_M : nullptr, false,
+                         (cudaStream_t)stream, "fwi_gradient");
+}
+
+int fwi_gradient_lanes(fwi_batch* b, double* grad_out, double* misfit_out, void* stream) {
+  return finish_gradient(b, grad_out, misfit_out, b ? b->m->d_M : nullptr, true,
+                         (cudaStream_t)stream, "fwi_gradient_lanes");
 }
 
 int fwi_batch_set_sources(fwi_batch* b, const double* src) {
@@ -1620,34 +1713,21 @@ int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes) {
   f += state * C;                       // checkpoints
   const int64_t r = m->p.grad_stride > 1 ? m->p.grad_stride : 1;
   f += N * S * (K / r);                 // recompute ring (subsampled levels only)
-  f += N;                               // FP32 gradient segment
+  f += N * S;                           // FP32 gradient segments (per shot)
   f += 2 * S * (nt + 1) * nrec + S * nt;  // records, residual, wavelet copies
-  *bytes = f * 4 + 2 * N * 8 + (int64_t)m->E * 4;
+  *bytes = f * 4 + 2 * N * S * 8 + (int64_t)m->E * 4;  // + compensated FP64 sums per shot
   return 0;
 }
 
 int fwi_gradient_raw(fwi_batch* b, double* dJdc_out, double* misfit_out, void* stream) {
-  if (!b || !dJdc_out) return fail(FWI_EINVAL, "fwi_gradient_raw: null argument");
-  if (int rc = check_device(b->m)) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int N = b->m->N;
-  double* out = dJdc_out;
-  const bool host = !is_device_ptr(dJdc_out);
-  if (host) {
-    if (!b->stage_grad && dalloc(&b->stage_grad, (size_t)N)) return FWI_ENOMEM;
-    out = b->stage_grad;
-  }
-  fwi::launch_finish_gradient(b->gsum, b->gcomp, nullptr, nullptr, b->m->d_mask, out, N, st);
-  g_launches += 1;
-  if (host) CUDA_TRY(cudaMemcpyAsync(dJdc_out, out, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st));
-  double J = 0;
-  CUDA_TRY(cudaMemcpyAsync(&J, b->misfit, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  if (misfit_out) *misfit_out = J;
-  CUDA_TRY(cudaMemsetAsync(b->gsum, 0, (size_t)N * sizeof(double), st));
-  CUDA_TRY(cudaMemsetAsync(b->gcomp, 0, (size_t)N * sizeof(double), st));
-  CUDA_TRY(cudaMemsetAsync(b->misfit, 0, sizeof(double), st));
-  CUDA_TRY(cudaStreamSynchronize(st));
+  return finish_gradient(b, dJdc_out, misfit_out, nullptr, false, (cudaStream_t)stream,
+                         "fwi_gradient_raw");
+}
+
+int fwi_batch_set_gradient_lanes(fwi_batch* b, int per_shot) {
+  if (!b || (per_shot != 0 && per_shot != 1))
+    return fail(FWI_EINVAL, "fwi_batch_set_gradient_lanes: per_shot must be 0 or 1");
+  b->grad_lanes = per_shot;
   return 0;
 }
 

@@ -9,9 +9,12 @@
 // behind the element phase. Phase 3 (chunk_store) finishes the owned DoFs from the table
 // and sends the halo DoFs' contributions to the global accumulators.
 //
-// Layer chunks add a third group (chunk_load_layer, issued once the layer indices are in the
-// table): the damping-layer auxiliaries P (and in the 3D forward Y) of every local layer DoF;
-// the element phase and the update read them from the table.
+// Layer chunks of steps without the gradient add a third group (chunk_load_layer, issued
+// once the layer indices are in the table): the damping-layer auxiliaries P (and in the 3D
+// forward Y) of every local layer DoF. Gradient steps, whose table is the largest, read P
+// from global memory (prefetched into L2 at the start of the element phase), so that two CTAs
+// still fit on an SM: with P in the table they ran at one CTA per SM and slower (542 against
+// 393 us per step on the KMV5 marine mesh).
 //
 // Layer chunks (two to four times the table of the others) skip group 1 and read v and
 // c1..c3 from global memory in phase 3, which keeps two of their CTAs on an SM.
@@ -19,8 +22,8 @@
 // Table layout (floats, shot-major [SG][Lm] with Lm odd so that the SG rows of one DoF fall
 // in different banks): u, y [SG][Lm]; c2 [Lm]; pi [Lm] (int); v [SG][Lm] and cf [3][Lm]
 // (not in layer chunks); gradient
-// steps: F [SG][Lm], g [Lm], cv [Lm]; layer chunks: s [D][SG][Lm], P [D][SG][Lm] (and in 3D
-// sY [D][SG][Lm], yw [SG][Lm], Yv [SG][Lm]).
+// steps: F [SG][Lm], g [SG][Lm], cv [Lm]; layer chunks: s [D][SG][Lm], P [D][SG][Lm] (not in
+// gradient steps) (and in 3D sY [D][SG][Lm], yw [SG][Lm], Yv [SG][Lm]).
 #pragma once
 #include "update.cuh"
 
@@ -45,8 +48,8 @@ __host__ __device__ inline int chunk_stride(int L) { return L | 1; }
 __host__ __device__ inline size_t chunk_tab_floats(int L, int SG, int D, bool grad, bool layer) {
   const size_t Lm = (size_t)chunk_stride(L);
   size_t f = Lm * (2 * (size_t)SG + 2) + (layer ? 0 : Lm * ((size_t)SG + 3));
-  if (grad) f += Lm * ((size_t)SG + 2);
-  if (layer) f += 2 * Lm * D * SG + (D == 3 ? Lm * D * SG + 2 * Lm * SG : 0);
+  if (grad) f += Lm * (2 * (size_t)SG + 1);
+  if (layer) f += (grad ? 1 : 2) * Lm * D * SG + (D == 3 ? Lm * D * SG + 2 * Lm * SG : 0);
   return f;
 }
 
@@ -68,12 +71,12 @@ __device__ __forceinline__ ChunkTab chunk_tab(float* base, int Lm, int SG, int D
   float* p0 = t.cf + (layer ? 0 : 3 * (size_t)Lm);
   float* p = p0;
   t.F = p;
-  t.g = t.F + (grad ? R : 0);
-  t.cv = t.g + (grad ? Lm : 0);
+  t.g = t.F + (grad ? R : 0);  // gradient integrand [SG][Lm] per shot, or row 0 for all
+  t.cv = t.g + (grad ? R : 0);
   p = t.cv + (grad ? Lm : 0);
   t.s = p;
   t.P = t.s + (layer ? (size_t)D * R : 0);
-  t.sY = t.P + (layer ? (size_t)D * R : 0);
+  t.sY = t.P + (layer && !grad ? (size_t)D * R : 0);
   t.yw = t.sY + (layer && D == 3 ? (size_t)D * R : 0);
   t.Yv = t.yw + (layer && D == 3 ? R : 0);
   return t;
@@ -141,7 +144,10 @@ __device__ __forceinline__ void chunk_load(const StepArgs& a, const ChunkDesc& c
     t.y[q * Lm + l] = 0.f;
   }
   if (GRAD)
-    for (int l = tid; l < cd.L; l += nth) t.g[l] = 0.f;
+    for (int i = tid; i < cd.L * SG; i += nth) {
+      const int l = i >> lg, q = i & (SG - 1);
+      t.g[q * Lm + l] = 0.f;
+    }
   if (LAYER) {
     for (int i = tid; i < Lm * D * SG; i += nth) {
       t.s[i] = 0.f;
@@ -195,6 +201,14 @@ __device__ __forceinline__ void chunk_prefetch_update(const StepArgs& a, const C
     const int pi = t.pi[l];
     if (pi >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.lcf + (size_t)pi * LC::COUNT));
   }
+  if (a.ring_u != nullptr) {  // gradient steps read P of every local layer DoF from global memory
+    for (int l = tid; l < cd.L; l += nth) {
+      const int pi = t.pi[l];
+      if (pi >= 0)
+#pragma unroll
+        for (int k = 0; k < D; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.P + ((size_t)pi * D + k) * a.S + s0));
+    }
+  }
   (void)SG;
 }
 
@@ -235,11 +249,11 @@ __device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& 
           sU[d] = t.s[(size_t)(d * SG + q) * Lm + l];
           sY[d] = 0.f;
           if constexpr (D == 3) sY[d] = t.sY[(size_t)(d * SG + q) * Lm + l];
-          po[d] = t.P[(size_t)(d * SG + q) * Lm + l];
+          po[d] = GRAD ? 0.f : t.P[(size_t)(d * SG + q) * Lm + l];
         }
         if constexpr (D == 3) ywv = t.yw[(size_t)q * Lm + l];
         dof_update_pre<D>(a, cd.own_lo + l, s, t.y[q * Lm + l], t.u[q * Lm + l], vo[k], c1[k], c2[k],
-                          c3[k], t.pi[l], sU, sY, ywv, po);
+                          c3[k], t.pi[l], sU, sY, ywv, GRAD ? nullptr : po);
       }
     }
   } else {
@@ -274,10 +288,19 @@ __device__ __forceinline__ void chunk_store(const StepArgs& a, const ChunkDesc& 
     }
   }
   if (GRAD) {
-    for (int l = tid; l < cd.L; l += nth) {
-      // several shot groups (blockIdx.y) add to the same DoF: atomics for all
-      const int dof = l < cd.own_n ? cd.own_lo + l : __ldg(a.halo + cd.hp + l - cd.own_n);
-      atomicAdd(a.gseg + dof, t.g[l]);
+    // fire-and-forget atomic adds (a plain read-modify-write of the owned DoFs would wait on
+    // each load: measured slower)
+    if (a.grad_lanes) {  // one segment accumulator per shot, [S][N]
+      for (int i = tid; i < cd.L * SG; i += nth) {
+        const int l = i >> lg, q = i & (SG - 1);
+        const int dof = l < cd.own_n ? cd.own_lo + l : __ldg(a.halo + cd.hp + l - cd.own_n);
+        atomicAdd(a.gseg + (size_t)(s0 + q) * a.N + dof, t.g[q * Lm + l]);
+      }
+    } else {  // summed over the shots (the element phase added every shot to row 0), [N]
+      for (int l = tid; l < cd.L; l += nth) {
+        const int dof = l < cd.own_n ? cd.own_lo + l : __ldg(a.halo + cd.hp + l - cd.own_n);
+        atomicAdd(a.gseg + dof, t.g[l]);
+      }
     }
   }
 }

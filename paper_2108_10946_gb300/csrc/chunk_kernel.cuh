@@ -92,7 +92,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
   cp_async_wait<1>();
   __syncthreads();
   if (layer) {
-    chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+    if (!grad) chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
     chunk_prefetch_update<D>(a, cd, t, SG, s0, tid, nth);
     cp_async_wait<0>();
     __syncthreads();
@@ -211,7 +211,7 @@ if constexpr (ROLL) {
                 g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
                 g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
         }
-        atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
+        atomicAdd(gloc + (a.grad_lanes ? sl * Lm : 0) + lqq, 2.f * t.cv[lqq] * wq * dot);
       }
       if (layer) {
         const int pi = piloc[lqq];
@@ -224,7 +224,7 @@ if constexpr (ROLL) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -242,7 +242,7 @@ if constexpr (ROLL) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = t.P[(size_t)(k * SG + sl) * Lm + lqq] *
+                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
                         __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)
@@ -336,7 +336,7 @@ if constexpr (ROLL) {
                 g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
                 g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
         }
-        atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
+        atomicAdd(gloc + (a.grad_lanes ? sl * Lm : 0) + lqq, 2.f * t.cv[lqq] * wq * dot);
       }
       if (layer) {
         const int pi = piloc[lqq];
@@ -349,7 +349,7 @@ if constexpr (ROLL) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -367,7 +367,7 @@ if constexpr (ROLL) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = t.P[(size_t)(k * SG + sl) * Lm + lqq] *
+                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
                         __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)
@@ -454,7 +454,7 @@ if constexpr (ROLL) {
                 g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
                 g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
         }
-        atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
+        atomicAdd(gloc + (a.grad_lanes ? sl * Lm : 0) + lqq, 2.f * t.cv[lqq] * wq * dot);
       }
       if (layer) {
         const int pi = piloc[lqq];
@@ -467,7 +467,7 @@ if constexpr (ROLL) {
 #pragma unroll
             for (int d = 0; d < D; ++d) acc += Am[d * D + k] * g[d];
             sq[k] = wq * acc;
-            const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
+            const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
             pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
           }
 #pragma unroll
@@ -485,7 +485,7 @@ if constexpr (ROLL) {
               float pw[3], fw[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k)
-                pw[k] = t.P[(size_t)(k * SG + sl) * Lm + lqq] *
+                pw[k] = (grad ? a.P[((size_t)pi * 3 + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq]) *
                         __ldg(lc + LC::PSI3 + k);
 #pragma unroll
               for (int d = 0; d < 3; ++d)
@@ -557,11 +557,14 @@ if constexpr (ROLL) {
     }
     float* yr = yloc + sl * Lm;
     float* ywr = ywloc + sl * Lm;
+    // the rolled forms take the shared-node indices back from shared memory, so that they
+    // need not stay in registers through the node loop
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
-      atomicAdd(yr + lq[q], y[q]);
+      const int lqq = ROLL || ROLL3 ? lqs[q * nth + tid] : lq[q];
+      atomicAdd(yr + lqq, y[q]);
       if constexpr (D == 3) {
-        if (layer && adj) atomicAdd(ywr + lq[q], yw[q]);
+        if (layer && adj) atomicAdd(ywr + lqq, yw[q]);
       }
     }
 #pragma unroll

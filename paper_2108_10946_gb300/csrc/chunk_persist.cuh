@@ -47,15 +47,15 @@ __host__ __device__ inline uint32_t pt_al16(uint32_t x) { return (x + 15u) & ~15
 // Byte offsets of the persistent kernel's dynamic shared memory.
 struct PtLayout {
   uint32_t rows, rows_dstride;  // Dhat rows [2][NN][NNP] floats; direction stride (floats)
-  uint32_t y, g;                // accumulators [Lmax][4] and [Lmax]
+  uint32_t y;                   // accumulator [Lmax][4]
   uint32_t meta0, meta_stride;  // 4 slots: descriptor (8 ints) + halo ids [Hmax]
   uint32_t buf0, buf_stride;    // 2 buffers
-  uint32_t bu, bF, bc2, bv, bcf, bcf_stride, bgeo, binj, blq;  // inside a buffer
+  uint32_t bu, bc2, bv, bcf, bcf_stride, bgeo, binj, blq;  // inside a buffer
   uint32_t total;
 };
 
 template <int NN, int NS>
-__host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax, bool grad) {
+__host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax) {
   constexpr int NNP = (NN + 3) / 4 * 4;
   PtLayout L{};
   uint32_t o = 0;
@@ -66,25 +66,19 @@ __host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax, bool
   o += pt_al16(4u * (2u * L.rows_dstride));
   L.y = o;
   o += pt_al16(16u * (uint32_t)Lmax);
-  L.g = o;
-  if (grad) o += pt_al16(4u * (uint32_t)Lmax);
   L.meta0 = o;
   L.meta_stride = pt_al16(32u + 4u * (uint32_t)Hmax);
   o += 4u * L.meta_stride;
   uint32_t b = 0;
   L.bu = b;
   b += pt_al16(16u * (uint32_t)Lmax);
-  L.bF = b;
-  if (grad) b += pt_al16(16u * (uint32_t)Lmax);
   L.bc2 = b;
   b += pt_al16(4u * (uint32_t)Lmax);
-  // the gradient steps read v and c1..c3 from global memory in the update phase (prefetched
-  // into L2 during the element phase), which keeps two CTAs per SM with the forward field
   L.bv = b;
-  if (!grad) b += pt_al16(16u * (uint32_t)Omax);
+  b += pt_al16(16u * (uint32_t)Omax);
   L.bcf = b;
   L.bcf_stride = pt_al16(4u * (uint32_t)Omax);
-  if (!grad) b += 3u * L.bcf_stride;
+  b += 3u * L.bcf_stride;
   L.bgeo = b;
   b += 3u * PT_PE * 4u;
   L.binj = b;
@@ -136,7 +130,7 @@ __device__ __forceinline__ void pt_issue_halo(const StepArgs& a, const PtLayout&
   for (int h = threadIdx.x; h < hn; h += PT_THREADS) cp_async4(ids + h, a.halo + hp + h);
 }
 
-template <int NS, bool GRAD>
+template <int NS>
 __device__ __forceinline__ void pt_issue_data(const StepArgs& a, const PtLayout& L, char* sm, int i,
                                               int nwork, int ngrp) {
   const PtItem it = pt_item(a, i, nwork, ngrp);
@@ -148,7 +142,6 @@ __device__ __forceinline__ void pt_issue_data(const StepArgs& a, const PtLayout&
   const int e0 = desc[0], own_lo = desc[2], own_n = desc[3], hn = desc[6] - desc[5];
   const int S = a.S, s0 = it.s0, t = threadIdx.x;
   float* bu = reinterpret_cast<float*>(B + L.bu);
-  float* bF = reinterpret_cast<float*>(B + L.bF);
   float* bv = reinterpret_cast<float*>(B + L.bv);
   float* bc2 = reinterpret_cast<float*>(B + L.bc2);
   for (int l = t; l < own_n; l += PT_THREADS) {
@@ -156,20 +149,15 @@ __device__ __forceinline__ void pt_issue_data(const StepArgs& a, const PtLayout&
     const size_t dof = (size_t)(own_lo + l);
     cp_async16(bu + 4 * l, a.u + gi);
     cp_async4(bc2 + l, a.c2 + dof);
-    if (GRAD) {
-      cp_async16(bF + 4 * l, a.ring_u + gi);
-    } else {
-      cp_async16(bv + 4 * l, a.v + gi);
+    cp_async16(bv + 4 * l, a.v + gi);
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        cp_async4(reinterpret_cast<float*>(B + L.bcf + r * L.bcf_stride) + l, a.cf + (size_t)r * a.N + dof);
-    }
+    for (int r = 0; r < 3; ++r)
+      cp_async4(reinterpret_cast<float*>(B + L.bcf + r * L.bcf_stride) + l, a.cf + (size_t)r * a.N + dof);
   }
   for (int h = t; h < hn; h += PT_THREADS) {
     const int id = ids[h];
     const size_t gi = (size_t)id * S + s0;
     cp_async16(bu + 4 * (own_n + h), a.u + gi);
-    if (GRAD) cp_async16(bF + 4 * (own_n + h), a.ring_u + gi);
     cp_async4(bc2 + own_n + h, a.c2 + id);
   }
   // per-element arrays of the chunk's 32 elements (rows padded to a multiple of 32 elements,
@@ -186,113 +174,6 @@ __device__ __forceinline__ void pt_issue_data(const StepArgs& a, const PtLayout&
   }
 }
 
-// Element phase of an adjoint step with the gradient integrand (Eq. gradient3): thread d of
-// an (element, shot) pair streams row q of Dhat_d twice, first for (Dhat_d lambda)_q and
-// (Dhat_d u)_q (the adjoint field in the table u, the forward field in F), then, once the
-// partner's values have arrived by shuffle, for its share of y = sum_q Dhat_q^T f_q. Direction
-// 0 adds 2 c_q w_q (grad lambda . Ghat grad u)(x_q) to the DoF's gradient accumulator.
-template <int NN, int NS>
-__device__ __forceinline__ void pt_element_grad(const StepArgs& a, const PtLayout& L, const float* rows,
-                                                const char* B, int d, int el, int sl, int s0, int e0,
-                                                int ne, int nsh, float* Y, float* Gacc) {
-  constexpr int NI = NN - NS;
-  constexpr int NNP = (NN + 3) / 4 * 4;
-  constexpr int NP = NNP / 2;
-  constexpr bool ROLL = NN >= 16;
-  const float* bu = reinterpret_cast<const float*>(B + L.bu);
-  const float* bF = reinterpret_cast<const float*>(B + L.bF);
-  const float* bc2 = reinterpret_cast<const float*>(B + L.bc2);
-  const float* bgeo = reinterpret_cast<const float*>(B + L.bgeo);
-  const int* binj = reinterpret_cast<const int*>(B + L.binj);
-  const unsigned short* blq = reinterpret_cast<const unsigned short*>(B + L.blq);
-  const bool act = el < ne;
-  const int s = s0 + sl;
-  const int lb = nsh + el * NI;
-  auto lidx = [&](int q) { return q < NS ? (act ? (int)blq[q * PT_PE + el] : 0) : (act ? lb + (q - NS) : 0); };
-  float2 U2[NP], F2[NP], y2[NP];
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    const int q0 = 2 * p, q1 = 2 * p + 1;
-    const int l0 = lidx(q0 < NN ? q0 : 0), l1 = lidx(q1 < NN ? q1 : 0);
-    U2[p].x = q0 < NN && act ? bu[4 * l0 + sl] : 0.f;
-    U2[p].y = q1 < NN && act ? bu[4 * l1 + sl] : 0.f;
-    F2[p].x = q0 < NN && act ? bF[4 * l0 + sl] : 0.f;
-    F2[p].y = q1 < NN && act ? bF[4 * l1 + sl] : 0.f;
-    y2[p] = make_float2(0.f, 0.f);
-  }
-  const float G0 = act ? bgeo[el] : 0.f, G1 = act ? bgeo[PT_PE + el] : 0.f;
-  const float G2 = act ? bgeo[2 * PT_PE + el] : 0.f;
-  const float Ga = d ? G1 : G0, Gb = d ? G2 : G1;
-  const int slot = act ? binj[el] : -1;
-  const float* rowd = rows + d * L.rows_dstride;
-#pragma unroll(ROLL ? 1 : NN)
-  for (int q = 0; q < NN; ++q) {
-    const float* rq = rowd + q * NNP;
-    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
-#pragma unroll
-    for (int j = 0; j < NNP / 4; ++j) {
-      const float4 r = *reinterpret_cast<const float4*>(rq + 4 * j);
-      a0 = __ffma2_rn(make_float2(r.x, r.y), U2[2 * j], a0);
-      a1 = __ffma2_rn(make_float2(r.z, r.w), U2[2 * j + 1], a1);
-      b0 = __ffma2_rn(make_float2(r.x, r.y), F2[2 * j], b0);
-      b1 = __ffma2_rn(make_float2(r.z, r.w), F2[2 * j + 1], b1);
-    }
-    const float2 sa = __fadd2_rn(a0, a1), sb = __fadd2_rn(b0, b1);
-    const float gd = sa.x + sa.y, hd = sb.x + sb.y;
-    const float go = __shfl_xor_sync(0xffffffffu, gd, 1);
-    const float ho = __shfl_xor_sync(0xffffffffu, hd, 1);
-    const float gx = d ? go : gd, gz = d ? gd : go;  // grad lambda at node q (reference)
-    const float hx = d ? ho : hd, hz = d ? hd : ho;  // grad u at node q (reference)
-    const int lqq = lidx(q);
-    const float c2v = bc2[lqq];
-    const float wq = c_w[q];
-    const float f = wq * c2v * (Ga * gx + Gb * gz);
-    if (d == 0 && act) {
-      const float dot = gx * (G0 * hx + G1 * hz) + gz * (G1 * hx + G2 * hz);
-      atomicAdd(Gacc + lqq, 2.f * sqrtf(c2v) * wq * dot);
-    }
-    const float2 ff = make_float2(f, f);
-#pragma unroll
-    for (int j = 0; j < NNP / 4; ++j) {
-      const float4 r = *reinterpret_cast<const float4*>(rq + 4 * j);
-      y2[2 * j] = __ffma2_rn(make_float2(r.x, r.y), ff, y2[2 * j]);
-      y2[2 * j + 1] = __ffma2_rn(make_float2(r.z, r.w), ff, y2[2 * j + 1]);
-    }
-  }
-  // adjoint sources at the receivers, in direction 0's partial sum
-  if (slot >= 0 && d == 0) {
-    const int rb = __ldg(a.rslot_ptr + slot), re = __ldg(a.rslot_ptr + slot + 1);
-    for (int r = rb; r < re; ++r) {
-      const float res = __ldg(a.resid + ((size_t)s * (a.nt + 1) + a.n) * a.R + __ldg(a.rslot_rec + r));
-#pragma unroll
-      for (int k = 0; k < NN; ++k) {
-        const float dv = res * __ldg(a.rslot_phi + (size_t)r * NN + k);
-        if (k & 1) y2[k >> 1].y += dv; else y2[k >> 1].x += dv;
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    float2 o;
-    o.x = __shfl_xor_sync(0xffffffffu, y2[p].x, 1);
-    o.y = __shfl_xor_sync(0xffffffffu, y2[p].y, 1);
-    y2[p] = __fadd2_rn(y2[p], o);
-  }
-  if (act) {
-    if (d == 0) {
-#pragma unroll
-      for (int q = 0; q < NS; ++q)
-        atomicAdd(Y + 4 * (int)blq[q * PT_PE + el] + sl, (q & 1) ? y2[q >> 1].y : y2[q >> 1].x);
-    } else {
-#pragma unroll
-      for (int j = 0; j < NI; ++j) {
-        const int q = NS + j;
-        Y[4 * (lb + j) + sl] = (q & 1) ? y2[q >> 1].y : y2[q >> 1].x;
-      }
-    }
-  }
-}
-
 template <int NN, int NS, int MODE>
 __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) {
   constexpr int NI = NN - NS;
@@ -300,8 +181,9 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
   constexpr bool ROLL = NN >= 16;
   constexpr bool GRAD = MODE == 2;
   constexpr bool ADJ = MODE != 0;
+  static_assert(!GRAD, "the gradient steps use the chunk kernel (faster there)");
   const int ngrp = a.S / PT_SG;
-  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max, GRAD);
+  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max);
   const int t = threadIdx.x;
   float* rows = reinterpret_cast<float*>(sm + L.rows);
   float4* Y4 = reinterpret_cast<float4*>(sm + L.y);
@@ -314,9 +196,6 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
     rows[idx] = (q < NN && j < NN) ? c_dhat[(d * NN + q) * NN + j] : 0.f;
   }
   for (int l = t; l < a.L_max; l += PT_THREADS) Y4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-  float* Gacc = reinterpret_cast<float*>(sm + L.g);  // gradient integrand per DoF (GRAD)
-  if (GRAD)
-    for (int l = t; l < a.L_max; l += PT_THREADS) Gacc[l] = 0.f;
 
   // prologue: descriptors of items 0, 1; halo ids of 0, 1 and descriptor of 2; data of 0
   pt_issue_desc(a, L, sm, 0, nwork, ngrp);
@@ -330,7 +209,7 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  pt_issue_data<NS, GRAD>(a, L, sm, 0, nwork, ngrp);
+  pt_issue_data<NS>(a, L, sm, 0, nwork, ngrp);
   cp_async_commit();
 
   const int d = t & 1, es = t >> 1, el = es & (PT_PE - 1), sl = es >> 5;
@@ -340,7 +219,7 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
     if (!it.valid) break;
     cp_async_wait<0>();
     __syncthreads();
-    pt_issue_data<NS, GRAD>(a, L, sm, i + 1, nwork, ngrp);
+    pt_issue_data<NS>(a, L, sm, i + 1, nwork, ngrp);
     pt_issue_halo(a, L, sm, i + 2, nwork, ngrp);
     pt_issue_desc(a, L, sm, i + 3, nwork, ngrp);
     cp_async_commit();
@@ -358,18 +237,7 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
     const unsigned short* blq = reinterpret_cast<const unsigned short*>(B + L.blq);
 
     // ---- element phase ------------------------------------------------------------------
-    if constexpr (GRAD) {
-      // the update phase reads v and c1..c3 from global memory: start bringing them to L2
-      for (int l = t; l < own_n; l += PT_THREADS) {
-        const size_t gi = (size_t)(own_lo + l) * a.S + it.s0;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.v + gi));
-        if ((l & 7) == 0) {
-#pragma unroll
-          for (int r = 0; r < 3; ++r) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.cf + (size_t)r * a.N + own_lo + l));
-        }
-      }
-      pt_element_grad<NN, NS>(a, L, rows, B, d, el, sl, it.s0, e0, ne, nsh, Y, Gacc);
-    } else {
+    {
       constexpr int NP = NNP / 2;  // node pairs (register pairs for the packed FMAs)
       const bool act = el < ne;
       const int e = e0 + el, s = it.s0 + sl;
@@ -479,13 +347,9 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
       const float* cf3 = reinterpret_cast<const float*>(B + L.bcf + 2 * L.bcf_stride);
       const int S = a.S;
       for (int l = t; l < own_n; l += PT_THREADS) {
-        const size_t dof = (size_t)(own_lo + l);
-        const float4 yv = Y4[l], uo = bu4[l];
-        const float4 vo = GRAD ? ld4(a.v + dof * S + it.s0) : bv4[l];
+        const float4 yv = Y4[l], uo = bu4[l], vo = bv4[l];
         Y4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float c1 = GRAD ? __ldg(a.cf + dof) : cf1[l];
-        const float c2 = GRAD ? __ldg(a.cf + (size_t)a.N + dof) : cf2[l];
-        const float c3 = GRAD ? __ldg(a.cf + 2 * (size_t)a.N + dof) : cf3[l];
+        const float c1 = cf1[l], c2 = cf2[l], c3 = cf3[l];
         float4 vn, un;
         vn.x = c1 * vo.x - c2 * yv.x - c3 * uo.x;
         vn.y = c1 * vo.y - c2 * yv.y - c3 * uo.y;
@@ -504,13 +368,6 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
         const float4 yv = Y4[own_n + h];
         Y4[own_n + h] = make_float4(0.f, 0.f, 0.f, 0.f);
         atomicAdd(reinterpret_cast<float4*>(a.r + (size_t)(ids[h] - a.N_own) * S + it.s0), yv);
-      }
-      if (GRAD) {  // the chunk's share of the FP32 gradient segment (several items add per DoF)
-        for (int l = t; l < own_n + hn; l += PT_THREADS) {
-          const int dof = l < own_n ? own_lo + l : ids[l - own_n];
-          atomicAdd(a.gseg + dof, Gacc[l]);
-          Gacc[l] = 0.f;
-        }
       }
     }
     __syncthreads();

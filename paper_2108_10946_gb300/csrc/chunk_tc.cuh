@@ -195,7 +195,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
     cp_async_wait<1>();  // the element phase's group
     __syncthreads();
     if (layer) {
-      chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
+      if (!grad) chunk_load_layer<D>(a, cd, t, Lm, SG, lg, s0, tid, nth);
       chunk_prefetch_update<D>(a, cd, t, SG, s0, tid, nth);
       cp_async_wait<0>();
       __syncthreads();
@@ -271,7 +271,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
           if (grad) {
             const float h0 = gfv[q], h1 = gfv[NN + q];
             const float dot = g0 * (Gm[0] * h0 + Gm[1] * h1) + g1 * (Gm[1] * h0 + Gm[2] * h1);
-            atomicAdd(gloc + lqq, 2.f * t.cv[lqq] * wq * dot);
+            atomicAdd(gloc + (a.grad_lanes ? sl * Lm : 0) + lqq, 2.f * t.cv[lqq] * wq * dot);
           }
           if (layer) {
             const int pi = t.pi[lqq];
@@ -281,7 +281,7 @@ __device__ __forceinline__ void chunk_tc_body(const StepArgs& a, float* smem, co
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
                 sq[k] = wq * (Am[0 * 2 + k] * g0 + Am[1 * 2 + k] * g1);
-                const float raw = t.P[(size_t)(k * SG + sl) * Lm + lqq];
+                const float raw = grad ? a.P[((size_t)pi * D + k) * S + s] : t.P[(size_t)(k * SG + sl) * Lm + lqq];
                 pq[k] = adj ? raw * __ldg(lc + LC::PSI2 + k) : raw;
               }
               f0 += wq * (Am[0] * pq[0] + Am[1] * pq[1]);

@@ -66,7 +66,8 @@ struct StepArgs {
   const float* resid;      // adjoint residual [S][nt+1][R]
   // gradient
   const float* ring_u;     // forward U^m [N][S] (null: no gradient this step)
-  float* gseg;             // [N] FP32 segment accumulator
+  float* gseg;             // FP32 segment accumulator: [S][N] per shot, or [N] summed
+  int grad_lanes;          // 1: per-shot gradient accumulators, 0: summed over the shots
   int* status;             // bit 0: non-finite value seen; bit 1: a bounded wait gave up
 };
 
@@ -99,9 +100,10 @@ void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, double sca
                  cudaStream_t st);
 void launch_finish_gradient(const double* gsum, const double* gcomp, const float* Minv_unused,
                             const double* M, const unsigned char* mask, double* out, int64_t N,
-                            cudaStream_t st);
-void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st);
+                            int lanes, int per_lane, cudaStream_t st);
+void launch_misfit(const float* resid, int64_t n, int lanes, double* acc, cudaStream_t st);
 void launch_residual(const float* d, const float* obs, float* res, int64_t n, cudaStream_t st);
+void launch_lane_reset(float* p, int64_t rows, int S, uint32_t mask, cudaStream_t st);
 int measure_fma_peak(double* tflops, int* sms);
 
 }  // namespace fwi

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(PT_THREADS, 2) k_chunk_pt(const StepArgs a, in
 template <int MODE>
 int launch_chunk_pt_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   if (nch <= 0) return 0;
-  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max, MODE == 2);
+  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max);
   if (L.total > 227u * 1024u) return -1;
   static size_t configured[64] = {0};
   static int per_sm[64] = {0}, nsm[64] = {0};

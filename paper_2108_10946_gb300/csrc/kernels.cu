@@ -68,30 +68,44 @@ void launch_fold(float* gseg, double* gsum, double* gcomp, int64_t N, double sca
   fold_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gseg, gsum, gcomp, N, scale);
 }
 
+// G = M^-1 g (Eq. gradient3) from the per-shot compensated sums (sum, comp) [lanes][N]: the
+// sum over the lanes (out [N]) or each lane's own (out [lanes][N]); zero where masked.
 __global__ void finish_kernel(const double* __restrict__ gsum, const double* __restrict__ gcomp,
                               const double* __restrict__ M, const unsigned char* __restrict__ mask,
-                              double* __restrict__ out, int64_t N) {
+                              double* __restrict__ out, int64_t N, int lanes, int per_lane) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   // M == nullptr: the raw discrete derivative dJ/dc (no division by the lumped mass)
-  const double g = gsum[i] - gcomp[i];
-  out[i] = mask[i] ? (M ? g / M[i] : g) : 0.0;
+  const double scale = M ? 1.0 / M[i] : 1.0;
+  const bool keep = mask[i] != 0;
+  double total = 0.0;
+  for (int s = 0; s < lanes; ++s) {
+    const double g = gsum[(size_t)s * N + i] - gcomp[(size_t)s * N + i];
+    if (per_lane)
+      out[(size_t)s * N + i] = keep ? (M ? g / M[i] : g) : 0.0;
+    else
+      total += g;
+  }
+  if (!per_lane) out[i] = keep ? total * scale : 0.0;
 }
 
 void launch_finish_gradient(const double* gsum, const double* gcomp, const float*,
                             const double* M, const unsigned char* mask, double* out, int64_t N,
-                            cudaStream_t st) {
+                            int lanes, int per_lane, cudaStream_t st) {
   if (N == 0) return;
-  finish_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gsum, gcomp, M, mask, out, N);
+  finish_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(gsum, gcomp, M, mask, out, N, lanes,
+                                                              per_lane);
 }
 
-// acc += 1/2 sum resid^2 (block reduction in FP64, one atomic per block)
+// acc[lane] += 1/2 sum resid^2 over each lane's n values (block reduction in FP64, one
+// atomic per block; blockIdx.y is the lane)
 __global__ void misfit_kernel(const float* __restrict__ r, int64_t n, double* acc) {
   __shared__ double part[256];
+  const float* rl = r + (size_t)blockIdx.y * n;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = r[i];
+    const double x = rl[i];
     s += x * x;
   }
   part[threadIdx.x] = s;
@@ -100,7 +114,22 @@ __global__ void misfit_kernel(const float* __restrict__ r, int64_t n, double* ac
     if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(acc, 0.5 * part[0]);
+  if (threadIdx.x == 0) atomicAdd(acc + blockIdx.y, 0.5 * part[0]);
+}
+
+// Zeroes the lanes named by mask (bit s = lane s) of a [rows][S] state array, S a power of
+// two: the lanes that start a new shot.
+__global__ void lane_reset_kernel(float* __restrict__ p, int64_t n, int S, uint32_t mask) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if ((mask >> (int)(i & (S - 1))) & 1u) p[i] = 0.f;
+}
+
+void launch_lane_reset(float* p, int64_t rows, int S, uint32_t mask, cudaStream_t st) {
+  const int64_t n = rows * S;
+  if (n == 0 || mask == 0) return;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  lane_reset_kernel<<<blocks, 256, 0, st>>>(p, n, S, mask);
 }
 
 __global__ void residual_kernel(const float* __restrict__ d, const float* __restrict__ obs,
@@ -173,10 +202,10 @@ int measure_fma_peak(double* tflops, int* sms) {
   return (int)e;
 }
 
-void launch_misfit(const float* resid, int64_t n, double* acc, cudaStream_t st) {
-  if (n == 0) return;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 1216);
-  misfit_kernel<<<blocks, 256, 0, st>>>(resid, n, acc);
+void launch_misfit(const float* resid, int64_t n, int lanes, double* acc, cudaStream_t st) {
+  if (n == 0 || lanes == 0) return;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, std::max(1, 1216 / lanes));
+  misfit_kernel<<<dim3(blocks, lanes), 256, 0, st>>>(resid, n, acc);
 }
 
 }  // namespace fwi

@@ -127,13 +127,13 @@ __device__ __forceinline__ void step_body(const StepArgs& a) {
               g[1] * (G[1] * gf[0] + G[3] * gf[1] + G[4] * gf[2]) +
               g[2] * (G[2] * gf[0] + G[4] * gf[1] + G[5] * gf[2]);
       }
-      float val = 2.f * __ldg(a.cvel + dq) * wq * dot;
-      for (int o = S >> 1; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-      if (valid && s == 0) {
-        if (q < NS)
-          atomicAdd(a.gseg + dq, val);
+      const float val = 2.f * __ldg(a.cvel + dq) * wq * dot;
+      if (valid) {  // per-shot segment accumulators [S][N], or one [N] for all shots
+        float* gs = a.gseg + (a.grad_lanes ? (size_t)s * a.N : 0);
+        if (q < NS || !a.grad_lanes)
+          atomicAdd(gs + dq, val);
         else
-          a.gseg[dq] += val;
+          gs[dq] += val;  // a bubble DoF of this element and shot: this thread only
       }
     }
     if (layer) {

@@ -69,12 +69,15 @@ def load():
         "fwi_forward_shot_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_adjoint_misfit": (ctypes.c_int, [_P, _P, _P]),
         "fwi_gradient": (ctypes.c_int, [_P, _P, _P, _P]),
+        "fwi_gradient_lanes": (ctypes.c_int, [_P, _P, _P, _P]),
+        "fwi_forward_segment": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint32, _P, _P, _P]),
         "fwi_batch_free": (ctypes.c_int, [_P]),
         "fwi_batch_set_sources": (ctypes.c_int, [_P, _P]),
         "fwi_batch_bytes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64)]),
         "fwi_gradient_raw": (ctypes.c_int, [_P, _P, _P, _P]),
         "fwi_profile": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
+        "fwi_batch_set_gradient_lanes": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_profile_read": (ctypes.c_int, [_P, _P, _P]),
         "fwi_mesh_free": (ctypes.c_int, [_P]),
         "fwi_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
@@ -317,6 +320,23 @@ class Batch:
         J = ctypes.c_double()
         _check(_lib.fwi_gradient(self._h, _ptr(out), ctypes.byref(J), _stream_ptr(stream)))
         return J.value
+
+    def forward_segment(self, nseg, reset_mask, wavelet, rec_out=None, stream=None):
+        """Advance every lane by nseg steps (lanes in reset_mask start a new shot first);
+        wavelet [S][nseg], rec_out [S][nseg+1][R] (host or device)."""
+        _check(_lib.fwi_forward_segment(self._h, int(nseg), ctypes.c_uint32(int(reset_mask)),
+                                        _ptr(wavelet), _ptr(rec_out), _stream_ptr(stream)))
+
+    def set_gradient_lanes(self, per_shot=True):
+        """Keep each shot's gradient apart in the next adjoint calls (for gradient_lanes)."""
+        _check(_lib.fwi_batch_set_gradient_lanes(self._h, int(bool(per_shot))))
+
+    def gradient_lanes(self, out, stream=None):
+        """out [S][N] float64 (host or device) = each shot's own gradient; returns the S
+        misfits J_s as a float64 array."""
+        J = np.zeros(self.S)
+        _check(_lib.fwi_gradient_lanes(self._h, _ptr(out), _ptr(J), _stream_ptr(stream)))
+        return J
 
     def set_wait_limit(self, polls):
         """Polls per bounded tensor-core wait (testing aid; -1 restores the default)."""

@@ -126,3 +126,52 @@ def test_config3_gradient_against_finite_differences(pkg):
     assert all(r[4] < 1e-2 for r in rows)
     b.close()
     m.close()
+
+
+def test_fwi_loop_reduces_misfit_and_model_error(pkg):
+    """Algorithm 1 end to end on the config-3 window: L-BFGS-B within [1, 5] km/s over the
+    library's misfit and gradient (two batches of four shots) from the 500 m-smoothed start
+    model. J must fall at every accepted iterate and the model error outside the masked
+    water and layer must shrink."""
+    from paper_2108_10946_gb300 import fwi
+    true = models.marine2d(0)
+    start = models.smoothed(true, 0.5)
+    f, k = 3.0, 3
+    box = (6.0, 8.0, 0.0, 1.5)
+    V, cells = meshes.adapted_tri(true, f, 15.0, box, seed=0, iters=10)
+    lay = dict(box=[(6.2, 7.8), (-10.0, 1.3)], faces=0b1011, width=0.2,
+               smax=signals.sigma_max(4.7, 0.2))
+    kw = dict(box=lay["box"], layer_faces=lay["faces"], layer_width=lay["width"],
+              sigma_max=lay["smax"], absorbing=True, water_speed=1.51)
+    probe = pkg.Mesh(V, cells, k, 1, dt=0.0, cfl_factor=0.8, **kw)
+    probe.set_velocity(true(probe.dof_coords()))
+    dt = probe.dt
+    probe.close()
+    nt = int(round(1.5 / dt))
+    m = pkg.Mesh(V, cells, k, nt, dt=dt, ckpt_stride=50, **kw)
+    xg = m.dof_coords()
+    ct, c0 = true(xg), start(xg)
+    m.set_velocity(ct)
+    recs = np.stack([np.linspace(6.1, 7.9, 40), np.full(40, 0.1)], 1)
+    batches, wavs, obs = [], [], []
+    for xs in (np.linspace(6.3, 7.7, 4), np.linspace(6.5, 7.5, 4)):
+        b = pkg.Batch(m, np.stack([xs, np.full(4, 0.05)], 1), recs)
+        w = torch.from_numpy(np.stack([signals.ricker_samples(f, dt, nt)] * 4)).float().cuda()
+        o = torch.zeros((4, nt + 1, len(recs)), device="cuda")
+        b.forward(w, o)
+        batches.append(b), wavs.append(w), obs.append(o)
+    shots = fwi.ShotSet(m, batches, wavs, obs)
+    c, hist = fwi.invert(shots, c0, bounds=(1.0, 5.0), maxiter=6)
+    free = (ct >= 1.51) & (xg[:, 0] > 6.2) & (xg[:, 0] < 7.8) & (xg[:, 1] < 1.3)
+    e0 = np.linalg.norm((c0 - ct)[free]) / np.linalg.norm(ct[free])
+    e1 = np.linalg.norm((c - ct)[free]) / np.linalg.norm(ct[free])
+    Js = [h["J"] for h in hist]
+    print(f"FWI: J {' -> '.join(f'{j:.4e}' for j in Js)} in {shots.evaluations} evaluations; "
+          f"model error {e0:.4%} -> {e1:.4%}")
+    assert all(b_ <= a_ for a_, b_ in zip(Js, Js[1:]))
+    assert Js[-1] < 0.7 * Js[0]
+    assert e1 < e0
+    assert np.all(c >= 1.0) and np.all(c <= 5.0)
+    for b in batches:
+        b.close()
+    m.close()

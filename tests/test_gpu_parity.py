@@ -311,3 +311,66 @@ def test_subsampled_gradient_matches_oracle(lib, r):
     assert err < GRAD_TOL
     assert rel_l2(out[1][0], Go_1) < GRAD_TOL
     assert out[r][1] < out[1][1]
+
+
+@pytest.mark.parametrize("form", [SIMT, TC, PLAIN], ids=["chunked", "tensor-cores", "plain"])
+def test_per_shot_gradients(lib, form):
+    """fwi_gradient_lanes returns each shot's own gradient M^-1 g_s and misfit J_s (the
+    per-shot terms of Eq. gradient3 that Section 4.5 sums over shots). Every lane matches the
+    oracle's gradient of that shot alone, the misfits match 1/2 |residual_s|^2, and the sum
+    over lanes equals fwi_gradient (the summed form) on a second identical adjoint solve (to
+    the FP32 summation-order noise of the atomics)."""
+    layout, tc = form
+    k, cfun = (4 if tc == 1 else 3), models.smooth2d  # the tensor-core step serves k = 4, 5
+    V, C, lay = _case2d(k, n=10, layer=True)
+    srcs = np.array([[0.5, 0.1], [0.2, 0.15], [0.8, 0.2], [0.35, 0.3]])
+    recs = np.array([[x, 0.9] for x in np.linspace(0.05, 0.95, 9)])
+    probe = OracleCase(V, C, k, cfun, 1.0, 1, layer=lay, absorbing=True)
+    dt = 0.8 * probe.ops.cfl_dt()
+    nt = int(round(0.5 / dt))
+    orc = OracleCase(V, C, k, cfun, dt, nt, layer=lay, absorbing=True)
+    box = [tuple(b) for b in lay["box"]]
+    mesh = lib.Mesh(V, C, k, nt, dt=dt, absorbing=True, ckpt_stride=13, box=box,
+                    layer_faces=lay["faces"], layer_width=lay["width"], sigma_max=lay["smax"],
+                    layout=layout, tensor_cores=tc)
+    xg = mesh.dof_coords()
+    perm = match_dofs(orc.mesh.coords, xg, 1.0)
+    mesh.set_velocity(cfun(xg))
+    wav = np.stack([signals.ricker_samples(8.0, dt, nt, t0=0.15) * (1 + 0.1 * i) for i in range(4)])
+    rng = np.random.default_rng(11)
+    res = (0.01 * rng.standard_normal((4, nt + 1, len(recs)))).astype(np.float32)
+    b = lib.Batch(mesh, srcs, recs)
+    rec = torch.zeros((4, nt + 1, len(recs)), device="cuda")
+    wav_d = torch.from_numpy(wav).float().cuda()
+    b.set_gradient_lanes(True)
+    b.forward(wav_d, rec)
+    b.adjoint(torch.from_numpy(res).cuda())
+    G = np.zeros((4, mesh.N))
+    J = b.gradient_lanes(G)
+    # the summed form (the default): its own accumulator, the same sum
+    b.set_gradient_lanes(False)
+    b.forward(wav_d, rec)
+    b.adjoint(torch.from_numpy(res).cuda())
+    Gsum = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+    Jsum = b.gradient(Gsum)
+    Gsum = Gsum.cpu().numpy()
+    for s in range(4):
+        Go = orc.gradient([srcs[s]], recs, [wav[s].astype(np.float32).astype(np.float64)],
+                          [res[s].astype(np.float64)])
+        err = rel_l2(G[s][perm], Go)
+        Jo = 0.5 * float(np.sum(res[s].astype(np.float64) ** 2))
+        print(f"form={form} shot {s}: lane gradient vs oracle rel-L2 {err:.3e}, J {J[s]:.6e} vs {Jo:.6e}")
+        assert err < GRAD_TOL
+        assert abs(J[s] - Jo) <= 1e-6 * Jo
+    serr = rel_l2(G.sum(0), Gsum)
+    print(f"form={form}: sum of lanes vs fwi_gradient rel-L2 {serr:.3e}")
+    # FP32 summation-order noise; the tensor-core adjoint's own error is larger (3xTF32)
+    assert serr < (2e-5 if tc == 1 else 5e-6) and abs(J.sum() - Jsum) <= 1e-12 * Jsum
+    # asking for lanes after a summed adjoint is an error, not a silent sum
+    b.forward(wav_d, rec)
+    b.adjoint(torch.from_numpy(res).cuda())
+    with pytest.raises(lib.FwiError):
+        b.gradient_lanes(G)
+    b.gradient(torch.zeros(mesh.N, dtype=torch.float64, device="cuda"))
+    b.close()
+    mesh.close()

@@ -132,7 +132,7 @@ def test_point_outside_the_mesh_is_refused_with_einval(dim):
 def test_batch_bytes_counts_every_device_array():
     """fwi_batch_bytes, the admission test of the shot server, against the sizes of the
     arrays a batch allocates (host-only mesh, no GPU): wavefields, layer auxiliaries,
-    checkpoints, the recompute ring, accumulators and the signal copies."""
+    checkpoints, the recompute ring, per-shot gradient accumulators and the signal copies."""
     import numpy as np
     from synth import meshes, signals
     V, C = meshes.structured_tri(12, 10, 1.2, 1.0, -0.1, 0.0)
@@ -149,8 +149,8 @@ def test_batch_bytes_counts_every_device_array():
     C_ = -(-nt // 7)
     state = S * (2 * N + Nl * 2)
     floats = (3 * N * S + 3 * Nl * 2 * S + 2 * Nl * S + 2 * N * S + Nl * 2 * S + Nl * S
-              + state * C_ + N * S * 7 + N + 2 * S * (nt + 1) * R + S * nt)
-    expect = floats * 4 + 2 * N * 8 + m.E * 4
+              + state * C_ + N * S * 7 + N * S + 2 * S * (nt + 1) * R + S * nt)
+    expect = floats * 4 + 2 * N * S * 8 + m.E * 4  # per-shot gradient sums
     assert m.batch_bytes(S, R) == expect
     m.close()
 
