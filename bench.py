@@ -372,7 +372,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def parity_sample(pkg, pool, info, k, S, T_par, workload="marine2d"):
+def parity_sample(pkg, pool, info, k, S, T_par, workload="marine2d", gstore=False):
     """The GPU library against the FP64 oracle on the workload's small marine window (same
     mesher, model, water, layer and absorbing boundary; S shots, T_par seconds): records
     rel-L2 (worst shot) and gradient rel-L2, as the tests measure them. The oracle shots run
@@ -393,6 +393,7 @@ def parity_sample(pkg, pool, info, k, S, T_par, workload="marine2d"):
     xg = mesh.dof_coords()
     mesh.set_velocity(small["model"](xg))
     b = pkg.Batch(mesh, srcs, small["recs"])
+    b.set_gradient_store(gstore)  # the bench's own gradient path
     rec = torch.zeros((S, nt + 1, len(small["recs"])), device="cuda")
     b.forward(torch.from_numpy(np.stack([wav] * S)).cuda(), rec)
     rec = rec.cpu().numpy()
@@ -486,6 +487,7 @@ def degree_line(pkg, k, args, S, fp32_tflops, sm_count, peaks, src):
     mesh = pkg.Mesh(wl["V"], wl["cells"], k, nt, dt=dt, **kw)
     mesh.set_velocity(c)
     b = pkg.Batch(mesh, wl["srcs"][:S], wl["recs"])
+    b.set_gradient_store(not args.no_gradient_store)
     R = len(wl["recs"])
     wav = torch.from_numpy(np.stack([signals.ricker_samples(5.0, dt, nt)] * S)).float().cuda()
     rec = torch.zeros((S, nt + 1, R), device="cuda")
@@ -565,6 +567,9 @@ def run_ours(args):
     S = args.shots
     shots = wl["srcs"][shots_for_rank(len(wl["srcs"]), S, rank, world)]
     batch = pkg.Batch(mesh, shots, wl["recs"])
+    # the gradient steps read the forward field's gradients stored by the recompute
+    # (fwi_batch_set_gradient_store; no effect on tetrahedra)
+    batch.set_gradient_store(not args.no_gradient_store)
     R = len(wl["recs"])
     wav = np.stack([signals.ricker_samples(wl["f"], dt, nt)] * S)
     wav_d = torch.from_numpy(wav).cuda()
@@ -691,7 +696,8 @@ def run_ours(args):
             # long enough for the sea-floor reflection (near 0.55 s) to reach the receivers,
             # so that the gradient below the masked water is more than rounding noise
             T_par = 0.6 if three_d else {2: 1.5, 3: 1.5, 4: 0.8, 5: 0.6}[wl["k"]]
-            parity = parity_sample(pkg, pool, info, wl["k"], S, T_par, args.workload)
+            parity = parity_sample(pkg, pool, info, wl["k"], S, T_par, args.workload,
+                                   gstore=not args.no_gradient_store)
             ob = oracle_rate(pool, wl["k"], info["dt"], cores, args.ref_steps, args.workload)
         finally:
             pool.close()
@@ -715,6 +721,7 @@ def run_ours(args):
                        "receivers": R, "ckpt_stride": args.ckpt, "C": wl["C"],
                        "l2": "inputs larger than L2 (wavefields of N*S floats, records)",
                        "parallelism": f"shots across {world} GPU(s), replicas of the mesh",
+                       "gradient_store": not args.no_gradient_store and not three_d,
                        "setup_s": setup_s},
             "e2e": {"value": e2e_val, "unit": "DoF-steps/s",
                     "h2d_bytes_per_step": int(wav.nbytes + obs_h.numel() * 4),
@@ -756,6 +763,9 @@ def main():
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream latency run")
+    ap.add_argument("--no-gradient-store", action="store_true",
+                    help="recompute the forward field's gradients in the gradient steps instead "
+                         "of storing them during the recompute (less device memory)")
     ap.add_argument("--serving-scale", type=float, default=1.0,
                     help="element-count factor of the serving pool (1 = 50k-2M triangles)")
     ap.add_argument("--extra-k", default="3,4",

@@ -271,6 +271,19 @@ int fwi_gradient_lanes(fwi_batch* b, double* grad_out, double* misfit_out, void*
  * FWI_EINVAL. The batch's device memory is sized for the per-shot form either way. */
 int fwi_batch_set_gradient_lanes(fwi_batch* b, int per_shot);
 
+/* Trades memory for arithmetic in the gradient steps (Eq. gradient3), for triangles in the
+ * chunked layout with a multiple of 4 shots, the summed gradient form and tensor_cores off
+ * (elsewhere the setting has no effect). With on = 1 the forward recompute of each adjoint
+ * segment also stores, per element, node, shot and direction, the forward field's
+ * (Ghat grad u) at the gradient levels, and the gradient steps read it back instead of
+ * contracting the forward field again (one more recompute step per segment gives the last
+ * level). The store takes (ckpt_stride / grad_stride) x (chunks without damping-layer
+ * elements) x (S / 4) x (nodes per element) x 1 KB of device memory, allocated by the
+ * next fwi_adjoint_* call (FWI_ENOMEM if it does not fit) and not counted by
+ * fwi_batch_bytes; on = 0 frees it. The results equal those without the store up to FP32
+ * summation order. */
+int fwi_batch_set_gradient_store(fwi_batch* b, int on);
+
 /* Per-kernel timing (tracing): when enabled, every time step of the batch's forward,
  * recompute and adjoint loops is bracketed by CUDA events on the call's stream. */
 int fwi_profile(fwi_batch* b, int enable);

@@ -197,6 +197,9 @@ struct fwi_batch {
   int tc_wait_limit = 1 << 22;  // polls of each bounded wait of the tensor-core kernel
   int grad_lanes = 0;           // 1: the next adjoint keeps each shot's gradient apart
   int acc_lanes = -1;           // what the accumulators hold: -1 nothing, 0 summed, 1 per shot
+  int gstore_on = 0;            // store the forward field's gradients during the recompute
+  float* gring = nullptr;       // [levels][gstore_level_floats] (allocated at first use)
+  size_t gring_level = 0;       // floats per level
   // optional per-kernel timing with CUDA events (fwi_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -1073,7 +1076,7 @@ int fwi_batch_free(fwi_batch* b) {
                   b->d_rslot_phi, b->d_rec_elem, b->d_rec_phi, b->u, b->v, b->r, b->P, b->Pacc,
                   b->PaccY, b->Y, b->Yacc, b->ua, b->va, b->Pa, b->Ya, b->ckpt, b->ring,
                   b->gseg, b->gsum, b->gcomp, b->misfit, b->status, b->wav_dev, b->rec_dev, b->res_dev, b->stage_in, b->stage_out,
-                  b->stage_grad};
+                  b->stage_grad, b->gring};
   for (void* p : ptrs) dfree(p);
   delete b;
   return 0;
@@ -1224,6 +1227,8 @@ StepArgs base_args(fwi_batch* b) {
   a.R = b->R;
   a.gseg = b->gseg;
   a.grad_lanes = b->grad_lanes;
+  a.gstore = nullptr;
+  a.gload = nullptr;
   a.status = b->status;
   a.tc_wait_limit = b->tc_wait_limit;
   return a;
@@ -1341,11 +1346,14 @@ int check_status(fwi_batch* b, cudaStream_t st) {
 
 // Forward steps n0 .. n1-1 on the batch's forward state; optional records and checkpoints.
 // window > 0: wav is [S][window] and recs [S][window+1][R] (the steps of one segment).
+// gstore: where the steps write the forward field's gradients (one step only).
 void forward_steps(fwi_batch* b, int n0, int n1, const float* wav, float* recs, bool ckpts,
-                   cudaStream_t st, float* r_scratch = nullptr, int window = 0) {
+                   cudaStream_t st, float* r_scratch = nullptr, int window = 0,
+                   float* gstore = nullptr) {
   StepArgs a = base_args(b);
   if (r_scratch) a.r = r_scratch;
   if (window > 0) a.nt = window;
+  a.gstore = gstore;
   a.mode = 0;
   a.tc = 0;  // forward and recompute steps always on FP32 CUDA cores (records within 1e-5)
   a.u = b->u;
@@ -1408,6 +1416,14 @@ int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
   if (b->acc_lanes >= 0 && b->acc_lanes != b->grad_lanes)
     return fail(FWI_EINVAL, "the gradient accumulators hold sums of the other kind: call "
                             "fwi_gradient* before changing fwi_batch_set_gradient_lanes");
+  // the gradient store: triangles on the persistent kernel, summed gradient form
+  const fwi_mesh* mc = b->m;
+  const bool gst = b->gstore_on && mc->dim == 2 && mc->layout == 0 && !mc->use_tc &&
+                   b->S % 4 == 0 && mc->nch0 > 0 && !b->grad_lanes;
+  if (gst && !b->gring) {
+    b->gring_level = fwi::gstore_level_floats(mc->nch0, b->S, mc->nn);
+    if (int rc = dalloc(&b->gring, b->gring_level * (size_t)(b->K / b->gstride))) return rc;
+  }
   b->acc_lanes = b->grad_lanes;
   const size_t rn = (size_t)b->S * (b->nt + 1) * b->R;
   fwi::launch_misfit(res, (int64_t)rn / b->S, b->S, b->misfit, st);
@@ -1431,12 +1447,17 @@ int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
     float *cu, *cv, *cP, *cY;
     ckpt_ptrs(b, c, &cu, &cv, &cP, &cY);
     if (int rc = copy_state(b, b->u, b->v, b->P, b->Y, cu, cv, cP, cY, st)) return rc;
-    // the ring keeps U^n for the levels n = 0 (mod r) of the segment (n0 is one of them)
+    // the ring keeps U^n for the levels n = 0 (mod r) of the segment (n0 is one of them);
+    // with the gradient store, the forward step from level n also writes the gradients of
+    // U^n for the persistent kernel's gradient step, and one more step (from level n1 - 1)
+    // gives those of the segment's last level
     const int r = b->gstride;
     CUDA_TRY(cudaMemcpyAsync(b->ring, b->u, NS_ * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    for (int n = n0; n < n1 - 1; ++n) {
-      forward_steps(b, n, n + 1, b->wav_dev, nullptr, false, st);
-      if ((n + 1) % r == 0)
+    auto glevel = [&](int n) { return b->gring + b->gring_level * (size_t)((n - n0) / r); };
+    for (int n = n0; n < (gst ? n1 : n1 - 1); ++n) {
+      forward_steps(b, n, n + 1, b->wav_dev, nullptr, false, st, nullptr, 0,
+                    gst && n % r == 0 ? glevel(n) : nullptr);
+      if (n + 1 < n1 && (n + 1) % r == 0)
         CUDA_TRY(cudaMemcpyAsync(b->ring + NS_ * (size_t)((n + 1 - n0) / r), b->u,
                                  NS_ * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
@@ -1444,6 +1465,7 @@ int adjoint_device(fwi_batch* b, const float* res, cudaStream_t st) {
       a.n = mm;
       // the gradient integrand at the subsampled levels only (the others: adjoint step alone)
       a.ring_u = mm % r == 0 ? b->ring + NS_ * (size_t)((mm - n0) / r) : nullptr;
+      a.gload = gst && mm % r == 0 ? glevel(mm) : nullptr;
       run_step(b, a, st);
     }
     fwi::launch_fold(b->gseg, b->gsum, b->gcomp, (int64_t)b->m->N * (b->grad_lanes ? b->S : 1),
@@ -1722,6 +1744,17 @@ int fwi_batch_bytes(const fwi_mesh* m, int nshots, int nrec, int64_t* bytes) {
 int fwi_gradient_raw(fwi_batch* b, double* dJdc_out, double* misfit_out, void* stream) {
   return finish_gradient(b, dJdc_out, misfit_out, nullptr, false, (cudaStream_t)stream,
                          "fwi_gradient_raw");
+}
+
+int fwi_batch_set_gradient_store(fwi_batch* b, int on) {
+  if (!b || (on != 0 && on != 1))
+    return fail(FWI_EINVAL, "fwi_batch_set_gradient_store: on must be 0 or 1");
+  b->gstore_on = on;
+  if (!on && b->gring) {
+    dfree(b->gring);
+    b->gring = nullptr;
+  }
+  return 0;
 }
 
 int fwi_batch_set_gradient_lanes(fwi_batch* b, int per_shot) {

@@ -26,6 +26,14 @@
 //
 // Table layouts in shared memory are DoF-major with the four shots contiguous ([L][4]), so
 // that one 16-byte copy moves a DoF's four shots and the update phase works on float4.
+//
+// Gradient steps (Eq. gradient3) from a stored forward field: the forward recompute steps of
+// an adjoint segment write, per (element, node q, shot, direction), h_d = (Ghat grad u)_d of
+// the forward field at that level (`gstore`, [item][q][shot][element][d]: one warp writes
+// 128 contiguous bytes per node). The gradient step of the same level reads it back
+// (`gload`): thread d has the adjoint's own g_d = (Dhat_d u_dag)_q, so the integrand
+// 2 c_q w_q (Ghat grad u) . grad u_dag is one product per thread and one shuffle per node,
+// instead of a second contraction over the forward field's nodal values.
 #pragma once
 #include "chunk_kernel.cuh"
 
@@ -34,6 +42,7 @@ namespace fwi {
 constexpr int PT_THREADS = 256;  // 32 elements x 4 shots x 2 directions
 constexpr int PT_PE = 32;        // elements per chunk (triangles)
 constexpr int PT_SG = 4;         // shots per work item
+static_assert(PT_SG * PT_PE * 2 == kGstoreNodeFloats, "stored-gradient layout");
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
@@ -48,6 +57,7 @@ __host__ __device__ inline uint32_t pt_al16(uint32_t x) { return (x + 15u) & ~15
 struct PtLayout {
   uint32_t rows, rows_dstride;  // Dhat rows [2][NN][NNP] floats; direction stride (floats)
   uint32_t y;                   // accumulator [Lmax][4]
+  uint32_t g;                   // gradient accumulator [Lmax] (gradient steps only)
   uint32_t meta0, meta_stride;  // 4 slots: descriptor (8 ints) + halo ids [Hmax]
   uint32_t buf0, buf_stride;    // 2 buffers
   uint32_t bu, bc2, bv, bcf, bcf_stride, bgeo, binj, blq;  // inside a buffer
@@ -55,7 +65,7 @@ struct PtLayout {
 };
 
 template <int NN, int NS>
-__host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax) {
+__host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax, bool grad = false) {
   constexpr int NNP = (NN + 3) / 4 * 4;
   PtLayout L{};
   uint32_t o = 0;
@@ -66,6 +76,8 @@ __host__ __device__ inline PtLayout pt_layout(int Lmax, int Omax, int Hmax) {
   o += pt_al16(4u * (2u * L.rows_dstride));
   L.y = o;
   o += pt_al16(16u * (uint32_t)Lmax);
+  L.g = o;
+  o += grad ? pt_al16(4u * (uint32_t)Lmax) : 0u;
   L.meta0 = o;
   L.meta_stride = pt_al16(32u + 4u * (uint32_t)Hmax);
   o += 4u * L.meta_stride;
@@ -174,6 +186,18 @@ __device__ __forceinline__ void pt_issue_data(const StepArgs& a, const PtLayout&
   }
 }
 
+// Gradient steps: bring item i's stored forward-field gradients (NN x 1 KB) to L2 while the
+// CTA still computes the item before it, so that the element phase's reads hit L2.
+template <int NN>
+__device__ __forceinline__ void pt_prefetch_gload(const StepArgs& a, int i, int nwork, int ngrp) {
+  const PtItem it = pt_item(a, i, nwork, ngrp);
+  if (!it.valid) return;
+  const float* base = a.gload + ((size_t)((it.c - a.ch0) * ngrp + it.s0 / PT_SG) * NN) * kGstoreNodeFloats;
+  constexpr int lines = NN * kGstoreNodeFloats * 4 / 128;
+  for (int l = threadIdx.x; l < lines; l += PT_THREADS)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (size_t)l * 32));
+}
+
 template <int NN, int NS, int MODE>
 __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) {
   constexpr int NI = NN - NS;
@@ -181,9 +205,8 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
   constexpr bool ROLL = NN >= 16;
   constexpr bool GRAD = MODE == 2;
   constexpr bool ADJ = MODE != 0;
-  static_assert(!GRAD, "the gradient steps use the chunk kernel (faster there)");
   const int ngrp = a.S / PT_SG;
-  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max);
+  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max, GRAD);
   const int t = threadIdx.x;
   float* rows = reinterpret_cast<float*>(sm + L.rows);
   float4* Y4 = reinterpret_cast<float4*>(sm + L.y);
@@ -196,6 +219,9 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
     rows[idx] = (q < NN && j < NN) ? c_dhat[(d * NN + q) * NN + j] : 0.f;
   }
   for (int l = t; l < a.L_max; l += PT_THREADS) Y4[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float* Gacc = reinterpret_cast<float*>(sm + L.g);
+  if (GRAD)
+    for (int l = t; l < a.L_max; l += PT_THREADS) Gacc[l] = 0.f;
 
   // prologue: descriptors of items 0, 1; halo ids of 0, 1 and descriptor of 2; data of 0
   pt_issue_desc(a, L, sm, 0, nwork, ngrp);
@@ -211,6 +237,7 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
   __syncthreads();
   pt_issue_data<NS>(a, L, sm, 0, nwork, ngrp);
   cp_async_commit();
+  if constexpr (GRAD) pt_prefetch_gload<NN>(a, 0, nwork, ngrp);
 
   const int d = t & 1, es = t >> 1, el = es & (PT_PE - 1), sl = es >> 5;
   bool bad = false;
@@ -223,6 +250,7 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
     pt_issue_halo(a, L, sm, i + 2, nwork, ngrp);
     pt_issue_desc(a, L, sm, i + 3, nwork, ngrp);
     cp_async_commit();
+    if constexpr (GRAD) pt_prefetch_gload<NN>(a, i + 1, nwork, ngrp);
 
     const char* meta = sm + L.meta0 + (i & 3) * L.meta_stride;
     const int* desc = reinterpret_cast<const int*>(meta);
@@ -266,8 +294,23 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
         }
       }
       const float* rowd = rows + d * L.rows_dstride;
+      // stored forward-field gradients of this item: written by forward steps (a.gstore set)
+      // and read by gradient steps, at [q][sl][el][d] with a stride of 256 floats per node
+      const size_t gofs = ((size_t)((it.c - a.ch0) * ngrp + it.s0 / PT_SG) * NN) * kGstoreNodeFloats +
+                          (size_t)(sl * PT_PE * 2 + el * 2 + d);
+      float* gst = MODE == 0 && a.gstore != nullptr ? a.gstore + gofs : nullptr;
+      const float* gld = GRAD ? a.gload + gofs : nullptr;
+      // two nodes ahead (read once: streaming loads)
+      float h1 = GRAD ? __ldcs(gld) : 0.f;
+      float h2 = GRAD && NN > 1 ? __ldcs(gld + kGstoreNodeFloats) : 0.f;
 #pragma unroll(ROLL ? 1 : NN)
       for (int q = 0; q < NN; ++q) {
+        float hq = 0.f;
+        if constexpr (GRAD) {
+          hq = h1;
+          h1 = h2;
+          if (q + 2 < NN) h2 = __ldcs(gld + (size_t)(q + 2) * kGstoreNodeFloats);
+        }
         float4 r4[NNP / 4];
 #pragma unroll
         for (int j = 0; j < NNP / 4; ++j) r4[j] = *reinterpret_cast<const float4*>(rowd + q * NNP + 4 * j);
@@ -284,7 +327,17 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
         const float gd = s2.x + s2.y;
         const float go = __shfl_xor_sync(0xffffffffu, gd, 1);
         const float gx = d ? go : gd, gz = d ? gd : go;
-        const float f = wc * (Ga * gx + Gb * gz);
+        const float h = Ga * gx + Gb * gz;  // (Ghat grad u)_d at node q
+        const float f = wc * h;
+        if (gst != nullptr) __stcs(gst + (size_t)q * kGstoreNodeFloats, h);  // read once, later
+        if constexpr (GRAD) {
+          // (Ghat grad u_fwd) . grad u_dag at node q: this direction's product, then the pair's sum
+          float part = hq * gd;
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          // 2 c_q w_q = 2 (w_q c_q^2) / c_q, with c_q from the reciprocal square root of c_q^2
+          // (a few 1e-8 relative; the gradient's bound is 1e-4)
+          if (d == 0 && act) atomicAdd(Gacc + lidx(q), 2.f * wc * rsqrtf(bc2[lidx(q)]) * part);
+        }
         const float2 ff = make_float2(f, f);
 #pragma unroll
         for (int j = 0; j < NNP / 4; ++j) {
@@ -368,6 +421,13 @@ __device__ __forceinline__ void pt_body(const StepArgs& a, char* sm, int nwork) 
         const float4 yv = Y4[own_n + h];
         Y4[own_n + h] = make_float4(0.f, 0.f, 0.f, 0.f);
         atomicAdd(reinterpret_cast<float4*>(a.r + (size_t)(ids[h] - a.N_own) * S + it.s0), yv);
+      }
+      if constexpr (GRAD) {  // the segment accumulator summed over the shots, [N]
+        for (int l = t; l < own_n + hn; l += PT_THREADS) {
+          const float g = Gacc[l];
+          Gacc[l] = 0.f;
+          atomicAdd(a.gseg + (l < own_n ? own_lo + l : ids[l - own_n]), g);
+        }
       }
     }
     __syncthreads();

@@ -17,6 +17,13 @@ namespace fwi {
 //                   e >= E0 (indexed e - E0)
 //   pidx   [N] index into the layer arrays or -1
 //   P, Pacc          [Nl][D][S], Y / Yacc [Nl][S] (3D)
+// Stored forward-field gradients (triangles, persistent kernel): per (chunk without layer
+// elements, group of 4 shots) item and node, 4 shots x 32 elements x 2 directions.
+constexpr int kGstoreNodeFloats = 256;
+inline size_t gstore_level_floats(int nch0, int S, int NN) {
+  return (size_t)nch0 * (size_t)(S / 4) * (size_t)NN * kGstoreNodeFloats;
+}
+
 struct StepArgs {
   int E, E0, S, Ns, N;
   int Es;              // row stride of the element arrays geo, lconn and inj: E rounded up to a
@@ -68,6 +75,8 @@ struct StepArgs {
   const float* ring_u;     // forward U^m [N][S] (null: no gradient this step)
   float* gseg;             // FP32 segment accumulator: [S][N] per shot, or [N] summed
   int grad_lanes;          // 1: per-shot gradient accumulators, 0: summed over the shots
+  float* gstore;           // forward steps: write the forward field's (Ghat grad u) here
+  const float* gload;      // gradient steps: read it back (persistent kernel, triangles)
   int* status;             // bit 0: non-finite value seen; bit 1: a bounded wait gave up
 };
 

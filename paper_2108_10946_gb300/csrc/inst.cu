@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(PT_THREADS, 2) k_chunk_pt(const StepArgs a, in
 template <int MODE>
 int launch_chunk_pt_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   if (nch <= 0) return 0;
-  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max);
+  const PtLayout L = pt_layout<NN, NS>(a.L_max, a.O_max, a.H_max, MODE == 2);
   if (L.total > 227u * 1024u) return -1;
   static size_t configured[64] = {0};
   static int per_sm[64] = {0}, nsm[64] = {0};
@@ -168,15 +168,20 @@ int launch_chunk(const StepArgs& a, cudaStream_t st, cudaStream_t stl) {
 #endif
 #if KMV_DIM == 2
   // triangles, four shots per work item: the persistent kernel takes the chunks without
-  // layer elements in the forward steps and the first adjoint step; the gradient steps and
-  // the layer chunks use the chunk kernel (its gradient form measured faster: 645 us against
-  // 799 us per step on the KMV5 marine mesh at S = 4)
-  if (mode != 2 && a.S % PT_SG == 0 && a.nch0 > 0) {
-    rc = mode == 0 ? launch_chunk_pt_t<0>(a, 0, a.nch0, st) : launch_chunk_pt_t<1>(a, 0, a.nch0, st);
+  // layer elements in the forward and adjoint steps, and in the gradient steps when the
+  // forward recompute stored the forward field's gradients (a.gload; summed gradient form);
+  // otherwise the gradient steps and the layer chunks use the chunk kernel. (The persistent
+  // kernel's gradient step needs more shared memory than its forward step, so if the forward
+  // step fell back to the chunk kernel, which stores nothing, so does the gradient step.)
+  if (a.S % PT_SG == 0 && a.nch0 > 0 && (mode != 2 || (a.gload != nullptr && !a.grad_lanes))) {
+    rc = mode == 0   ? launch_chunk_pt_t<0>(a, 0, a.nch0, st)
+         : mode == 1 ? launch_chunk_pt_t<1>(a, 0, a.nch0, st)
+                     : launch_chunk_pt_t<2>(a, 0, a.nch0, st);
     if (rc > 0) return rc;
     if (rc == 0) {
       if (mode == 0) return launch_chunk_t<0, true>(a, a.nch0, a.nch - a.nch0, stl);
-      return launch_chunk_t<1, true>(a, a.nch0, a.nch - a.nch0, stl);
+      if (mode == 1) return launch_chunk_t<1, true>(a, a.nch0, a.nch - a.nch0, stl);
+      return launch_chunk_t<2, true>(a, a.nch0, a.nch - a.nch0, stl);
     }
     rc = 0;  // the tables do not fit: the chunk kernel below takes every chunk
   }

@@ -78,6 +78,7 @@ def load():
         "fwi_profile": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_batch_set_gradient_lanes": (ctypes.c_int, [_P, ctypes.c_int]),
+        "fwi_batch_set_gradient_store": (ctypes.c_int, [_P, ctypes.c_int]),
         "fwi_profile_read": (ctypes.c_int, [_P, _P, _P]),
         "fwi_mesh_free": (ctypes.c_int, [_P]),
         "fwi_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
@@ -330,6 +331,11 @@ class Batch:
     def set_gradient_lanes(self, per_shot=True):
         """Keep each shot's gradient apart in the next adjoint calls (for gradient_lanes)."""
         _check(_lib.fwi_batch_set_gradient_lanes(self._h, int(bool(per_shot))))
+
+    def set_gradient_store(self, on=True):
+        """Store the forward field's gradients during the recompute (faster gradient steps,
+        more device memory; see fwi_batch_set_gradient_store)."""
+        _check(_lib.fwi_batch_set_gradient_store(self._h, int(bool(on))))
 
     def gradient_lanes(self, out, stream=None):
         """out [S][N] float64 (host or device) = each shot's own gradient; returns the S
