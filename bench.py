@@ -76,8 +76,8 @@ def make_workload3d(k=2, seed=0, small=False, scale=1.0):
     """The 3D workload (inputs only): the 5 km x 5 km x 3 km thrust model (layered, a thrust-
     folded interface, two 5.5-6.0 km/s lenses, smooth perturbation; seeded stand-in for
     Overthrust3D) with a 0.75 km damping layer on the sides and bottom, on a depth-graded
-    Kuhn tetrahedral mesh (40 m boxes in the top kilometre of slow rock, 60 m below; about
-    4.9M tetrahedra), 16 shots in a 4 x 4 grid at 50 m depth and a 100 x 100 receiver grid at
+    Kuhn tetrahedral mesh (59 m boxes across, 40 m deep in the top kilometre of slow rock,
+    60 m below; 5.08M tetrahedra), 16 shots in a 4 x 4 grid at 50 m depth and a 100 x 100 receiver grid at
     100 m depth, 5 Hz, 3 s. small=True: a 1.2 km x 1.2 km x 1.0 km box of the same model
     (the oracle's sample). scale < 1 coarsens the boxes by that factor (for profiler
     captures of the same kernels on a smaller case)."""
@@ -93,7 +93,7 @@ def make_workload3d(k=2, seed=0, small=False, scale=1.0):
         recs = np.array([[x, y, 0.1] for x in g for y in g])
         lay = dict(box=[(2.05, 2.95), (2.05, 2.95), (-10.0, 0.85)], faces=0b101111, width=0.15)
     else:
-        xs = np.linspace(-L, 5 + L, int(round(108 * scale)) + 1)
+        xs = np.linspace(-L, 5 + L, int(round(110 * scale)) + 1)
         zs = np.concatenate([np.arange(0.0, 1.0, 0.04 / scale),
                              np.arange(1.0, 3.0 + L + 1e-9, 0.06 / scale)])
         V, cells = meshes.kuhn_tets(xs, xs, zs)
@@ -540,7 +540,7 @@ def run_ours(args):
     pool = info = None
     cores = host_cores()
     three_d = args.workload == "thrust3d"
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's worker pool starts now (spawn) and builds its window while the GPU runs
         pool = oracle_pool(args.k, cores, args.workload)
     fp32_tflops, sm_count = pkg.lib.fp32_peak()
@@ -649,12 +649,14 @@ def run_ours(args):
                                   "three launches of one forward step on this mesh")
 
     extra_k = []
-    if rank == 0 and args.extra_k and not three_d:
+    # the side measurements (other degrees, plain form, serving) belong to the one-GPU line;
+    # multi-GPU lines measure the scaled step alone
+    if rank == 0 and world == 1 and args.extra_k and not three_d:
         for kx in [int(x) for x in args.extra_k.split(",") if x]:
             extra_k.append(degree_line(pkg, kx, args, S, fp32_tflops, sm_count, peaks, src))
 
     plain = None
-    if args.plain:
+    if args.plain and world == 1:
         # the unfused form: layout 1 (one thread per element and shot, global atomics,
         # separate node kernel), one shot per launch, same window
         mp_ = pkg.Mesh(wl["V"], wl["cells"], wl["k"], nt, dt=dt, box=lay["box"],
@@ -686,7 +688,7 @@ def run_ours(args):
         mp_.close()
 
     serving = None
-    if rank == 0 and not args.no_serving and not three_d:
+    if rank == 0 and world == 1 and not args.no_serving and not three_d:
         serving = serving_stream(pkg, scale=args.serving_scale)
 
     cpu = parity = None

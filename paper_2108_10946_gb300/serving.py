@@ -11,7 +11,8 @@ Two kinds of job:
 
 * rolling forward batches. Forward-only requests of a mesh share one batch whose lanes
   advance together in segments of ``segment`` time steps (``fwi_forward_segment``; by default
-  the mesh's checkpoint stride). At every segment boundary the lanes whose shots have reached
+  the mesh's checkpoint stride or a 16th of the record, whichever is longer), sized for the
+  waiting requests plus one spare lane. At every segment boundary the lanes whose shots have reached
   the end of their record are handed back, and pending requests start in the free lanes
   (their state reset in the same call), so a request joins a batch that is part way through
   other shots' records instead of waiting for them to finish.
@@ -138,9 +139,11 @@ class ShotServer:
         return best
 
     def _demand(self, name):
-        """Lanes a new rolling batch of mesh `name` would fill now."""
+        """Lanes for a new rolling batch of mesh `name`: the forward requests it would fill
+        now plus one spare lane (a request arriving during the record joins it at the next
+        boundary instead of starting a batch of its own), at most max_batch."""
         n = sum(1 for r in self.pending[name] if not r.wants_gradient)
-        return max(1, min(self.max_batch, n - self.rolling_free[name]))
+        return max(1, min(self.max_batch, n - self.rolling_free[name] + 1))
 
     def _acquire(self, name, S):
         """A resident batch of mesh `name` with S lanes or fewer: an idle one of the largest
@@ -300,7 +303,9 @@ class ShotServer:
     def _run_rolling(self, name, mesh, recs, key, batch, src0, stream):
         S = key[1]
         nt, R = mesh.nsteps, len(recs)
-        nseg = self.segment or getattr(mesh.params, "ckpt_stride", 0) or 50
+        # default segment: the checkpoint stride, or a 16th of the record if that is longer
+        # (every boundary costs a host round trip; a 16th keeps admission waits short)
+        nseg = self.segment or max(getattr(mesh.params, "ckpt_stride", 0) or 50, -(-nt // 16))
         nseg = max(1, min(int(nseg), nt))
         lanes = [None] * S  # [request, own time step t] per lane
         srcs = np.tile(np.asarray(src0, dtype=np.float64), (S, 1))  # idle lanes: any point inside

@@ -123,3 +123,48 @@ def test_tensor_core_wait_that_gives_up_returns_etimedout(pkg):
     assert rel < 1e-5  # the same computation; only the order of the atomic sums differs
     b.close()
     mesh.close()
+
+
+def test_invalid_arguments_of_the_batch_calls_return_einval(pkg):
+    """Host-side argument checks of the serving and gradient calls: a segment of 0 steps or
+    longer than the mesh's record, a reset mask naming a lane beyond the batch, an adjoint
+    before any forward solve, per-shot gradients after a summed adjoint, a gradient-mode
+    change while the accumulators hold sums of the other kind. Each returns FWI_EINVAL
+    before any launch, and the batch keeps working."""
+    from paper_2108_10946_gb300.lib import FWI_EINVAL, FwiError
+    V, C = meshes.structured_tri(8, 8)
+    probe = pkg.Mesh(V, C, 2, 1, dt=0.0, cfl_factor=0.8)
+    probe.set_velocity(models.smooth2d(probe.dof_coords()))
+    dt = probe.dt
+    probe.close()
+    nt = 40
+    mesh = pkg.Mesh(V, C, 2, nt, dt=dt, ckpt_stride=10)
+    mesh.set_velocity(models.smooth2d(mesh.dof_coords()))
+    b = pkg.Batch(mesh, np.array([[0.5, 0.3], [0.3, 0.4]]), np.array([[0.4, 0.8], [0.6, 0.8]]))
+    wav = np.stack([signals.ricker_samples(8.0, dt, nt)] * 2).astype(np.float32)
+    rec = np.zeros((2, nt + 1, 2), np.float32)
+
+    def einval(call):
+        with pytest.raises(FwiError) as ei:
+            call()
+        assert ei.value.code == FWI_EINVAL
+
+    einval(lambda: b.adjoint(np.zeros((2, nt + 1, 2), np.float32)))  # no forward yet
+    einval(lambda: b.forward_segment(0, 0, wav[:, :1], None))
+    einval(lambda: b.forward_segment(nt + 1, 0, np.zeros((2, nt + 1), np.float32), None))
+    einval(lambda: b.forward_segment(5, 0b100, wav[:, :5], None))  # lane 2 of a 2-lane batch
+    b.forward(wav, rec)
+    b.adjoint(0.1 * rec)
+    einval(lambda: b.gradient_lanes(np.zeros((2, mesh.N))))  # the adjoint summed the shots
+    b.set_gradient_lanes(True)
+    b.forward(wav, rec)
+    einval(lambda: b.adjoint(0.1 * rec))  # accumulators still hold the summed form
+    G = np.zeros(mesh.N)
+    b.gradient(G)  # clears them
+    b.forward(wav, rec)
+    b.adjoint(0.1 * rec)
+    Gl = np.zeros((2, mesh.N))
+    J = b.gradient_lanes(Gl)
+    assert np.all(np.isfinite(Gl)) and np.all(J > 0)
+    b.close()
+    mesh.close()
