@@ -150,9 +150,9 @@ def test_invalid_arguments_of_the_batch_calls_return_einval(pkg):
         assert ei.value.code == FWI_EINVAL
 
     einval(lambda: b.adjoint(np.zeros((2, nt + 1, 2), np.float32)))  # no forward yet
-    einval(lambda: b.forward_segment(0, 0, wav[:, :1], None))
+    einval(lambda: b.forward_segment(0, 0, np.ascontiguousarray(wav[:, :1]), None))
     einval(lambda: b.forward_segment(nt + 1, 0, np.zeros((2, nt + 1), np.float32), None))
-    einval(lambda: b.forward_segment(5, 0b100, wav[:, :5], None))  # lane 2 of a 2-lane batch
+    einval(lambda: b.forward_segment(5, 0b100, np.ascontiguousarray(wav[:, :5]), None))  # lane 2 of 2
     b.forward(wav, rec)
     b.adjoint(0.1 * rec)
     einval(lambda: b.gradient_lanes(np.zeros((2, mesh.N))))  # the adjoint summed the shots
