@@ -12,7 +12,7 @@ Two kinds of job:
 * rolling forward batches. Forward-only requests of a mesh share one batch whose lanes
   advance together in segments of ``segment`` time steps (``fwi_forward_segment``; by default
   the mesh's checkpoint stride or a 16th of the record, whichever is longer), sized for the
-  waiting requests plus one spare lane. At every segment boundary the lanes whose shots have reached
+  waiting requests. At every segment boundary the lanes whose shots have reached
   the end of their record are handed back, and pending requests start in the free lanes
   (their state reset in the same call), so a request joins a batch that is part way through
   other shots' records instead of waiting for them to finish.
@@ -140,10 +140,11 @@ class ShotServer:
 
     def _demand(self, name):
         """Lanes for a new rolling batch of mesh `name`: the forward requests it would fill
-        now plus one spare lane (a request arriving during the record joins it at the next
-        boundary instead of starting a batch of its own), at most max_batch."""
+        now, at most max_batch (rounded up to a power of two by the caller; the lanes that
+        leaves free take requests arriving during the record). A spare lane on top was
+        measured slower: an idle lane costs about as much as a busy one."""
         n = sum(1 for r in self.pending[name] if not r.wants_gradient)
-        return max(1, min(self.max_batch, n - self.rolling_free[name] + 1))
+        return max(1, min(self.max_batch, n - self.rolling_free[name]))
 
     def _acquire(self, name, S):
         """A resident batch of mesh `name` with S lanes or fewer: an idle one of the largest

@@ -81,7 +81,7 @@ def test_idle_batches_of_other_meshes_are_evicted():
 def test_gradient_requests_share_a_batch_and_forward_requests_roll():
     """Gradient requests of one mesh pack into one batch (each lane returns its own
     gradient); a forward request starts a rolling batch of its mesh sized by the forward
-    demand plus one spare lane, after which as many of that mesh's forward requests as the batch has free lanes
+    demand, after which as many of that mesh's forward requests as the batch has free lanes
     wait for its segment boundaries instead of new jobs."""
     srv = server({"a": FakeMesh(1), "b": FakeMesh(1)}, budget=1000, max_batch=4, rolling=True)
     srv.pending["a"].append(req(0, "a", 5.0))
@@ -94,16 +94,16 @@ def test_gradient_requests_share_a_batch_and_forward_requests_roll():
     assert (kind, name, key) == ("batch", "b", ("b", 4)) and [r.rid for r in reqs] == [1, 2, 4]
     assert [r.rid for r in srv.pending["b"]] == [3, 5]
     kind, name, key, _, reqs, src = srv._take()
-    assert (kind, name, key, reqs) == ("roll", "b", ("b", 4), []) and srv.rolling_free["b"] == 4
+    assert (kind, name, key, reqs) == ("roll", "b", ("b", 2), []) and srv.rolling_free["b"] == 2
     kind, name, key, _, _, _ = srv._take()
-    assert (kind, name, key) == ("roll", "a", ("a", 2))
+    assert (kind, name, key) == ("roll", "a", ("a", 1))
     assert srv._take() is None  # b's forward requests wait for its rolling batch
     assert [r.rid for r in srv._admit("b", 2)] == [3, 5]
     # a third forward request of b beyond the free lanes starts another rolling batch
     srv.rolling_free["b"] = 0
     srv.pending["b"].append(req(6, "b", 7.0))
     kind, name, key, _, _, _ = srv._take()
-    assert (kind, name, key) == ("roll", "b", ("b", 2))
+    assert (kind, name, key) == ("roll", "b", ("b", 1))
 
 
 def test_rolling_admission_yields_to_older_requests_of_other_meshes():
