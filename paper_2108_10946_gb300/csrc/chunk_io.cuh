@@ -199,7 +199,14 @@ __device__ __forceinline__ void chunk_prefetch_update(const StepArgs& a, const C
       for (int r = 0; r < 3; ++r) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.cf + (size_t)r * a.N + dof));
     }
     const int pi = t.pi[l];
-    if (pi >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.lcf + (size_t)pi * LC::COUNT));
+    if (pi >= 0) {
+      const float* lc = a.lcf + (size_t)pi * LC::COUNT;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(lc));
+      if constexpr (D == 3) {  // 88-byte records may straddle two lines; the omega state Y
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(lc + LC::COUNT - 1));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Y + (size_t)pi * a.S + s0));
+      }
+    }
   }
   if (a.ring_u != nullptr) {  // gradient steps read P of every local layer DoF from global memory
     for (int l = tid; l < cd.L; l += nth) {
