@@ -627,8 +627,16 @@ def run_ours(args):
         batch.forward(wav_h.numpy(), rec_h.numpy())
         batch.adjoint_misfit(obs_h.numpy())
         batch.gradient(G_h.numpy())
+        if dist is not None:  # the shots' gradient summed over the ranks, as in the step
+            G_d.copy_(G_h)
+            dist.all_reduce(G_d)
+            G_h.copy_(G_d)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
     e2e_val = S * N * nt * 2 * world / e2e_s
 
     # per-kernel timing of the forward and adjoint steps (events on the library's stream)
@@ -726,8 +734,8 @@ def run_ours(args):
                        "gradient_store": not args.no_gradient_store and not three_d,
                        "setup_s": setup_s},
             "e2e": {"value": e2e_val, "unit": "DoF-steps/s",
-                    "h2d_bytes_per_step": int(wav.nbytes + obs_h.numel() * 4),
-                    "d2h_bytes_per_step": int(rec_h.numel() * 4 + N * 8)},
+                    "h2d_bytes_per_step": int(wav.nbytes + obs_h.numel() * 4 + (N * 8 if world > 1 else 0)),
+                    "d2h_bytes_per_step": int(rec_h.numel() * 4 + N * 8 * (2 if world > 1 else 1))},
             "gpu_launches": int(launches),
             "roofline": roof,
             "parity_vs_oracle": parity,
