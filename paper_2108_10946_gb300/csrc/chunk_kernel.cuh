@@ -25,15 +25,16 @@ namespace fwi {
 // register allocator keep the operands in aligned pairs.
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Threads per (element, shot): KMV3 tetrahedra in damping-layer chunks split the node loop
+// Threads per (element, shot): tetrahedra in damping-layer chunks split the node loop
 // between two threads, so that a CTA holds twice the threads for the same chunk table (those
 // tables, with the layer's auxiliaries, allow two CTAs per SM). The two halves are whole
 // warps, each taking every other quadrature node, so constant-bank reads stay warp-uniform.
 // Measured on the thrust model at half scale: KMV3 layer steps 34 % (forward) and 31 %
-// (adjoint) faster. Chunks without layer elements keep one thread (the split raised their
-// registers more than it added threads), and so do KMV2 tetrahedra (adjoint 6 % slower).
-template <int D, int NN, bool LAYER>
-__host__ __device__ constexpr int chunk_qsplit() { return D == 3 && NN >= 32 && LAYER ? 2 : 1; }
+// (adjoint) faster, KMV2 forward steps 5.5 % faster (its adjoint steps were 6 % slower split
+// and keep one thread). Chunks without layer elements keep one thread (the split raised
+// their registers more than it added threads).
+template <int D, int NN, int MODE, bool LAYER>
+__host__ __device__ constexpr int chunk_qsplit() { return D == 3 && LAYER && (NN >= 32 || MODE == 0) ? 2 : 1; }
 
 // floats of dynamic shared memory per CTA for a chunk table of L entries and SG shots
 // (plus, for the rolled per-node loop, the per-thread local connectivity and, for triangles
@@ -110,7 +111,7 @@ __device__ __forceinline__ void chunk_body(const StepArgs& a, float* smem) {
 
   // ---- 2. elements ---------------------------------------------------------------------
   const int P = a.PE;
-  constexpr int QS = chunk_qsplit<D, NN, LAYER>();
+  constexpr int QS = chunk_qsplit<D, NN, MODE, LAYER>();
   const int nq = nth / QS;  // threads of one half: (element, shot) pairs
   const int half = QS > 1 ? tid / nq : 0;
   const int tq = tid - half * nq;

@@ -64,7 +64,7 @@ int launch_chunk_t(const StepArgs& a, int ch0, int nch, cudaStream_t st) {
   StepArgs b = a;
   b.ch0 = ch0;
   dim3 grid((unsigned)nch, (unsigned)(a.S / a.SG));
-  k_chunk<MODE, LAYER><<<grid, a.PE * a.SG * chunk_qsplit<D, NN, LAYER>(), bytes, st>>>(b);
+  k_chunk<MODE, LAYER><<<grid, a.PE * a.SG * chunk_qsplit<D, NN, MODE, LAYER>(), bytes, st>>>(b);
   return 0;
 }
 
